@@ -1,0 +1,324 @@
+/*
+ * CPU oracle for the Hough-transform track finder — TEST INFRASTRUCTURE ONLY.
+ * Only tests/, the smoke check and the bench's CPU-baseline leg use it; it
+ * shares nothing with the GPU library.  Build with
+ *   gcc -O2 -ffp-contract=off -fno-fast-math -fPIC -shared -pthread
+ * (-ffp-contract=off matters: gcc on aarch64 would otherwise fuse a*b+c).
+ *
+ * Paper: Lujan et al., "GPU Enhancement of the Trigger to Extend Physics Reach
+ * at the LHC" (arXiv:1311.2769).  Section 3 defines the Hough transform used
+ * here: zero votes everywhere, one vote per (datum, containing instance),
+ * local maxima = features, then hits are attached to the features found.
+ */
+#include "ht_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+static const double kPi = 3.14159265358979323846;
+
+/* Bin centres (Section 3: the parameter space is a grid of feature
+ * instances; each instance is represented by its cell centre). */
+void hto_tables(const hto_grid *g, float *cos_phi, float *sin_phi, float *d0)
+{
+    for (int32_t i = 0; i < g->n_phi; ++i) {
+        double phi = ((double)i + 0.5) * (2.0 * kPi / (double)g->n_phi);
+        cos_phi[i] = (float)cos(phi);
+        sin_phi[i] = (float)sin(phi);
+    }
+    for (int32_t j = 0; j < g->n_d0; ++j) {
+        double w = ((double)g->d0_max - (double)g->d0_min) / (double)g->n_d0;
+        d0[j] = (float)((double)g->d0_min + ((double)j + 0.5) * w);
+    }
+}
+
+/*
+ * Track model (Section 3 asks for curved, displaced tracks, i.e. three
+ * parameters): the circle with perigee d0 n, n = (-sin phi0, cos phi0),
+ * tangent t = (cos phi0, sin phi0) and signed curvature kappa.  Requiring the
+ * hit h to lie on it gives
+ *     kappa = 2 (q - d0) / (r^2 + d0^2 - 2 d0 q),   q = h . n = y cos phi0 - x sin phi0,
+ * whose denominator is |h - P|^2.  The bin coordinate is
+ *     w = (kappa - kappa_min) * n_kappa / (kappa_max - kappa_min),
+ * and the hit votes into bin floor(w) when den > 0 and 0 <= w < n_kappa.
+ * Every operation below is one binary64 IEEE operation in this order.
+ */
+double hto_w64(const hto_grid *g, float xf, float yf, float cf, float sf, float df)
+{
+    double x = xf, y = yf, c = cf, s = sf, d = df;
+    double q = (y * c) - (x * s);
+    double a = q - d;
+    double den = (((x * x) + (y * y)) + (d * d)) - ((2.0 * d) * q);
+    if (!(den > 0.0))
+        return NAN;
+    double kappa = (2.0 * a) / den;
+    double scale = (double)g->n_kappa / ((double)g->kappa_max - (double)g->kappa_min);
+    return (kappa - (double)g->kappa_min) * scale;
+}
+
+int32_t hto_kbin_at(const hto_grid *g, float x, float y, float c, float s, float d)
+{
+    double w = hto_w64(g, x, y, c, s, d);
+    if (!(w >= 0.0 && w < (double)g->n_kappa))
+        return -1;
+    return (int32_t)w;
+}
+
+void hto_kbin_cells(const hto_grid *g, int64_t n, const float *x, const float *y, const float *c,
+                    const float *s, const float *d, int32_t *out)
+{
+    for (int64_t t = 0; t < n; ++t)
+        out[t] = hto_kbin_at(g, x[t], y[t], c[t], s[t], d[t]);
+}
+
+/* Bin centre tables are rebuilt per call: slow and plain on purpose. */
+int32_t hto_kbin(const hto_grid *g, float x, float y, int32_t i, int32_t j)
+{
+    double phi = ((double)i + 0.5) * (2.0 * kPi / (double)g->n_phi);
+    double w = ((double)g->d0_max - (double)g->d0_min) / (double)g->n_d0;
+    float d = (float)((double)g->d0_min + ((double)j + 0.5) * w);
+    return hto_kbin_at(g, x, y, (float)cos(phi), (float)sin(phi), d);
+}
+
+/* The same formula with float32 operations in a fixed order (IEEE division,
+ * no contraction).  Not part of the method's definition: it is the form whose
+ * bins are compared against the binary64 ones to report the flip fraction. */
+int32_t hto_kbin_fp32(const hto_grid *g, float x, float y, float c, float s, float d)
+{
+    double scale = (double)g->n_kappa / ((double)g->kappa_max - (double)g->kappa_min);
+    float S2 = (float)(2.0 * scale);
+    float H = (float)(-(double)g->kappa_min * scale);
+    float r2 = (x * x) + (y * y);
+    float q = (y * c) - (x * s);
+    float a = q - d;
+    float n = a * S2;
+    float den = (r2 + (d * d)) - ((d + d) * q);
+    if (!(den > 0.0f))
+        return -1;
+    float v = n / den;
+    float wv = v + H;
+    if (!(wv >= 0.0f && wv < (float)g->n_kappa))
+        return -1;
+    return (int32_t)wv;
+}
+
+/* Section 3 voting: every hit adds one vote to each instance containing it. */
+static void vote_event(const hto_grid *g, const float *cphi, const float *sphi, const float *d0,
+                       const float *x, const float *y, int64_t n_hits, uint32_t *acc1)
+{
+    const int64_t nd = g->n_d0, nk = g->n_kappa;
+    memset(acc1, 0, sizeof(uint32_t) * (size_t)g->n_phi * (size_t)nd * (size_t)nk);
+    for (int64_t h = 0; h < n_hits; ++h)
+        for (int32_t i = 0; i < g->n_phi; ++i)
+            for (int32_t j = 0; j < g->n_d0; ++j) {
+                int32_t k = hto_kbin_at(g, x[h], y[h], cphi[i], sphi[i], d0[j]);
+                if (k >= 0)
+                    acc1[((int64_t)i * nd + j) * nk + k] += 1u;
+            }
+}
+
+static void tables_alloc(const hto_grid *g, float **c, float **s, float **d)
+{
+    *c = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    *s = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    *d = (float *)malloc(sizeof(float) * (size_t)g->n_d0);
+    hto_tables(g, *c, *s, *d);
+}
+
+void hto_vote(const hto_grid *g, const float *x, const float *y,
+              const int32_t *event_offsets, int32_t n_events, uint32_t *acc)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    const int64_t cells = (int64_t)g->n_phi * g->n_d0 * g->n_kappa;
+    for (int32_t e = 0; e < n_events; ++e) {
+        int64_t lo = event_offsets[e], hi = event_offsets[e + 1];
+        vote_event(g, c, s, d, x + lo, y + lo, hi - lo, acc + (int64_t)e * cells);
+    }
+    free(c); free(s); free(d);
+}
+
+void hto_vote_column(const hto_grid *g, const float *x, const float *y, int64_t n_hits,
+                     int32_t i, int32_t j, uint32_t *out)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    memset(out, 0, sizeof(uint32_t) * (size_t)g->n_kappa);
+    for (int64_t h = 0; h < n_hits; ++h) {
+        int32_t k = hto_kbin_at(g, x[h], y[h], c[i], s[i], d[j]);
+        if (k >= 0)
+            out[k] += 1u;
+    }
+    free(c); free(s); free(d);
+}
+
+/*
+ * Section 3: "local maxima in the parameter space".  A cell at or above the
+ * threshold is a peak when it is strictly greater than every neighbour that
+ * precedes it in linear (phi, d0, kappa) order and at least as large as every
+ * neighbour that follows it.  Neighbours are the distinct cells other than
+ * itself at offsets {-1, 0, 1}^3; phi0 is periodic, d0 and kappa are not.
+ */
+int32_t hto_is_peak(const hto_grid *g, const uint32_t *acc1, uint32_t threshold,
+                    int32_t i, int32_t j, int32_t k)
+{
+    const int64_t nd = g->n_d0, nk = g->n_kappa;
+    const int64_t self = ((int64_t)i * nd + j) * nk + k;
+    const uint32_t v = acc1[self];
+    if (v < threshold)
+        return 0;
+    for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int dk = -1; dk <= 1; ++dk) {
+                int32_t ii = ((i + di) % g->n_phi + g->n_phi) % g->n_phi;
+                int32_t jj = j + dj, kk = k + dk;
+                if (jj < 0 || jj >= g->n_d0 || kk < 0 || kk >= g->n_kappa)
+                    continue;
+                int64_t other = ((int64_t)ii * nd + jj) * nk + kk;
+                if (other == self)
+                    continue;
+                uint32_t u = acc1[other];
+                if (other < self ? !(v > u) : !(v >= u))
+                    return 0;
+            }
+    return 1;
+}
+
+int64_t hto_peaks(const hto_grid *g, const uint32_t *acc, int32_t n_events,
+                  uint32_t threshold, hto_peak *out, int64_t cap)
+{
+    const int64_t cells = (int64_t)g->n_phi * g->n_d0 * g->n_kappa;
+    int64_t n = 0;
+    for (int32_t e = 0; e < n_events; ++e) {
+        const uint32_t *a1 = acc + (int64_t)e * cells;
+        for (int32_t i = 0; i < g->n_phi; ++i)
+            for (int32_t j = 0; j < g->n_d0; ++j)
+                for (int32_t k = 0; k < g->n_kappa; ++k)
+                    if (hto_is_peak(g, a1, threshold, i, j, k)) {
+                        if (n < cap) {
+                            hto_peak p = {e, i, j, k, a1[((int64_t)i * g->n_d0 + j) * g->n_kappa + k]};
+                            out[n] = p;
+                        }
+                        ++n;
+                    }
+    }
+    return n;
+}
+
+/*
+ * Hits of a candidate (Section 3: the maxima become reconstructed tracks,
+ * which a confirmation fit then uses): hit h of the peak's event belongs to
+ * peak (i, j, k) when it votes in column (i, j) and its bin lies within
+ * `window` bins of k.
+ */
+int64_t hto_associate(const hto_grid *g, const float *x, const float *y,
+                      const int32_t *event_offsets, const hto_peak *peaks, int64_t n_peaks,
+                      int32_t window, int64_t *peak_offsets, int32_t *hit_idx, int64_t cap)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    int64_t n = 0;
+    peak_offsets[0] = 0;
+    for (int64_t p = 0; p < n_peaks; ++p) {
+        const hto_peak *pk = &peaks[p];
+        int64_t lo = event_offsets[pk->event], hi = event_offsets[pk->event + 1];
+        for (int64_t h = lo; h < hi; ++h) {
+            int32_t kb = hto_kbin_at(g, x[h], y[h], c[pk->i_phi], s[pk->i_phi], d[pk->i_d0]);
+            if (kb >= 0 && abs(kb - pk->i_kappa) <= window) {
+                if (n < cap)
+                    hit_idx[n] = (int32_t)h;
+                ++n;
+            }
+        }
+        peak_offsets[p + 1] = n;
+    }
+    free(c); free(s); free(d);
+    return n;
+}
+
+void hto_flip_count(const hto_grid *g, const float *x, const float *y,
+                    const int32_t *event_offsets, int32_t n_events, int64_t *out)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    int64_t v64 = 0, v32 = 0, diff = 0;
+    for (int64_t h = event_offsets[0]; h < event_offsets[n_events]; ++h)
+        for (int32_t i = 0; i < g->n_phi; ++i)
+            for (int32_t j = 0; j < g->n_d0; ++j) {
+                int32_t k64 = hto_kbin_at(g, x[h], y[h], c[i], s[i], d[j]);
+                int32_t k32 = hto_kbin_fp32(g, x[h], y[h], c[i], s[i], d[j]);
+                v64 += k64 >= 0;
+                v32 += k32 >= 0;
+                diff += k64 != k32;
+            }
+    out[0] = v64; out[1] = v32; out[2] = diff;
+    free(c); free(s); free(d);
+}
+
+/* ---- event-parallel harness (timing only; the per-event work is the plain code above) ---- */
+
+typedef struct {
+    const hto_grid *g;
+    const float *x, *y;
+    const int32_t *offs;
+    int32_t n_events, stride, first;
+    uint32_t threshold;
+    int32_t window;
+    int64_t votes, peaks, pairs;
+} run_arg;
+
+static void *run_worker(void *p)
+{
+    run_arg *a = (run_arg *)p;
+    const hto_grid *g = a->g;
+    const int64_t cells = (int64_t)g->n_phi * g->n_d0 * g->n_kappa;
+    uint32_t *acc1 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cells);
+    int64_t pcap = 1 << 16;
+    hto_peak *pk = (hto_peak *)malloc(sizeof(hto_peak) * (size_t)pcap);
+    for (int32_t e = a->first; e < a->n_events; e += a->stride) {
+        int64_t lo = a->offs[e], hi = a->offs[e + 1];
+        int32_t offs1[2] = {0, (int32_t)(hi - lo)};
+        hto_vote(g, a->x + lo, a->y + lo, offs1, 1, acc1);
+        for (int64_t c = 0; c < cells; ++c)
+            a->votes += acc1[c];
+        int64_t np = hto_peaks(g, acc1, 1, a->threshold, pk, pcap);
+        if (np > pcap) {
+            pcap = np;
+            pk = (hto_peak *)realloc(pk, sizeof(hto_peak) * (size_t)pcap);
+            np = hto_peaks(g, acc1, 1, a->threshold, pk, pcap);
+        }
+        a->peaks += np;
+        int64_t *po = (int64_t *)malloc(sizeof(int64_t) * (size_t)(np + 1));
+        a->pairs += hto_associate(g, a->x + lo, a->y + lo, offs1, pk, np, a->window, po, NULL, 0);
+        free(po);
+    }
+    free(pk);
+    free(acc1);
+    return NULL;
+}
+
+void hto_run_events(const hto_grid *g, const float *x, const float *y,
+                    const int32_t *event_offsets, int32_t n_events,
+                    uint32_t threshold, int32_t window, int32_t n_threads, int64_t *out)
+{
+    if (n_threads < 1)
+        n_threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    run_arg *args = (run_arg *)calloc((size_t)n_threads, sizeof(run_arg));
+    for (int32_t t = 0; t < n_threads; ++t) {
+        run_arg a = {g, x, y, event_offsets, n_events, n_threads, t, threshold, window, 0, 0, 0};
+        args[t] = a;
+        pthread_create(&th[t], NULL, run_worker, &args[t]);
+    }
+    out[0] = out[1] = out[2] = 0;
+    for (int32_t t = 0; t < n_threads; ++t) {
+        pthread_join(th[t], NULL);
+        out[0] += args[t].votes;
+        out[1] += args[t].peaks;
+        out[2] += args[t].pairs;
+    }
+    free(args);
+    free(th);
+}

@@ -1,0 +1,107 @@
+/*
+ * CPU oracle for the Hough-transform track finder — TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded C statement of what the GPU library computes,
+ * used by the tests, the smoke check and the CPU-baseline leg of the bench to
+ * judge the CUDA path.  It shares no code, header, table or constant with the
+ * library (include/ht.h, paper_1311_2769_gb300/csrc) and neither links the
+ * other.  Nothing on the product path may call it.
+ *
+ * Method (Lujan et al., "GPU Enhancement of the Trigger to Extend Physics Reach
+ * at the LHC", Section 3): every parameter instance starts with zero votes;
+ * each hit adds one vote to every instance that contains it; local maxima of
+ * the vote array are track candidates.  The instances are the cells of a
+ * (phi0, d0, kappa) perigee-helix grid — the curved, displaced 3-parameter
+ * model Section 3 calls for — whose two 2-parameter special cases (d0 = 0:
+ * curved tracks through the origin; kappa = 0: straight displaced tracks) are
+ * the models the paper's own implementation used.
+ *
+ * Precision: the curvature bin of a (hit, phi0, d0) column is defined by one
+ * fixed sequence of IEEE-754 binary64 operations on the float32 hit
+ * coordinates and float32 bin-centre tables (see ht_oracle.c); compile with
+ * -ffp-contract=off so no FMA is formed.
+ */
+#ifndef HT_ORACLE_H
+#define HT_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t n_phi, n_d0, n_kappa;
+    float d0_min, d0_max, kappa_min, kappa_max;
+} hto_grid;
+
+typedef struct {
+    int32_t event, i_phi, i_d0, i_kappa;
+    uint32_t votes;
+} hto_peak;
+
+/* Bin-centre tables: cos/sin of phi_i = (i + 1/2) 2pi / n_phi and
+ * d0_j = d0_min + (j + 1/2)(d0_max - d0_min)/n_d0, each rounded to float once. */
+void hto_tables(const hto_grid *g, float *cos_phi, float *sin_phi, float *d0);
+
+/* Curvature bin of hit (x, y) in column (i, j) by the binary64 definition;
+ * -1 when the hit casts no vote in that column. */
+int32_t hto_kbin(const hto_grid *g, float x, float y, int32_t i, int32_t j);
+
+/* Same, but with the column's table values given directly. */
+int32_t hto_kbin_at(const hto_grid *g, float x, float y, float c, float s, float d);
+
+/* The binary64 value w = (kappa - kappa_min) * n_kappa / (kappa_max - kappa_min)
+ * for (hit, column), or NaN when den <= 0 (used by the filter-bound tests). */
+double hto_w64(const hto_grid *g, float x, float y, float c, float s, float d);
+
+/* hto_kbin_at for n independent cells (plain loop; used by tests). */
+void hto_kbin_cells(const hto_grid *g, int64_t n, const float *x, const float *y, const float *c,
+                    const float *s, const float *d, int32_t *out);
+
+/* Plain float32 op-order bin (IEEE division, no contraction): the form whose
+ * disagreement with hto_kbin is reported as the flip fraction. */
+int32_t hto_kbin_fp32(const hto_grid *g, float x, float y, float c, float s, float d);
+
+/* Vote every event: acc is [n_events][n_phi][n_d0][n_kappa] uint32, zeroed here. */
+void hto_vote(const hto_grid *g, const float *x, const float *y,
+              const int32_t *event_offsets, int32_t n_events, uint32_t *acc);
+
+/* One (phi, d0) column of one event: out[n_kappa], zeroed here. */
+void hto_vote_column(const hto_grid *g, const float *x, const float *y, int64_t n_hits,
+                     int32_t i, int32_t j, uint32_t *out);
+
+/* Local maxima at or above threshold, ascending (event, linear index).
+ * Returns the number of peaks found (may exceed cap; only cap are written). */
+int64_t hto_peaks(const hto_grid *g, const uint32_t *acc, int32_t n_events,
+                  uint32_t threshold, hto_peak *out, int64_t cap);
+
+/* Is cell (i, j, k) of one event's accumulator a peak? */
+int32_t hto_is_peak(const hto_grid *g, const uint32_t *acc1, uint32_t threshold,
+                    int32_t i, int32_t j, int32_t k);
+
+/* Hit-to-candidate association (CSR).  peak_offsets has n_peaks + 1 entries;
+ * hit_idx receives global hit indices, ascending within each peak.  Returns
+ * the number of pairs (may exceed cap; only cap are written). */
+int64_t hto_associate(const hto_grid *g, const float *x, const float *y,
+                      const int32_t *event_offsets, const hto_peak *peaks, int64_t n_peaks,
+                      int32_t window, int64_t *peak_offsets, int32_t *hit_idx, int64_t cap);
+
+/* Flip metric over all (hit, column) pairs of the given events:
+ * out[0] = binary64 votes, out[1] = float32 votes, out[2] = columns whose
+ * bins differ (a vote in one form and none, or another bin, in the other). */
+void hto_flip_count(const hto_grid *g, const float *x, const float *y,
+                    const int32_t *event_offsets, int32_t n_events, int64_t *out);
+
+/* Whole path per event (vote, peaks, associate) on n_threads host threads,
+ * one event at a time per thread, results reduced to counts:
+ * out[0] = votes cast, out[1] = peaks, out[2] = pairs.  Used to time the
+ * oracle as a CPU baseline. */
+void hto_run_events(const hto_grid *g, const float *x, const float *y,
+                    const int32_t *event_offsets, int32_t n_events,
+                    uint32_t threshold, int32_t window, int32_t n_threads, int64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
