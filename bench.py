@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark: events/s of the whole Hough-transform path on one GB300.
+
+One step = vote + peaks + association of one batch of 4096 ragged synthetic
+trigger events (tracks/event lognormal, median 150; 256 x 32 x 128 grid;
+threshold 9, window 1), run as one persistent launch per kernel replayed from
+a CUDA graph.  Inputs are resident in HBM when the timed region starts;
+the L2 is flushed between timed steps.  Also reported: the plain
+one-event-per-launch form on a sample of the same batch, the end-to-end
+rate through the C ABI with pinned host buffers (copies inside the timed
+region), the vote kernel against its issue-rate roofline, and the CPU oracle
+on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun each rank processes its own batch (weak scaling, no collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch_4096_lognormal"
+METRIC = "events/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(w, batch, budget_s=15.0, max_events=None):
+    """The oracle as it stands, event-parallel on every host core, on a bounded
+    prefix of the workload's events (sized to about budget_s seconds)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # calibrate on one small batch, then size the sample
+    n = min(cores, batch.n_events)
+    sub = batch.select(range(n))
+    t0 = time.perf_counter()
+    oracle.run_events(w.grid, sub.x, sub.y, sub.event_offsets, w.threshold, w.window, cores)
+    dt = time.perf_counter() - t0
+    per_event = dt * cores / n
+    want = int(max(n, min(batch.n_events, budget_s * cores / max(per_event, 1e-9))))
+    if max_events:
+        want = min(want, max_events)
+    sub = batch.select(range(want))
+    t0 = time.perf_counter()
+    votes, peaks, pairs = oracle.run_events(w.grid, sub.x, sub.y, sub.event_offsets, w.threshold, w.window, cores)
+    dt = time.perf_counter() - t0
+    return {"value": want / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"events 0..{want - 1} of the 4096-event batch ({sub.n_hits} hits), "
+                      f"vote+peaks+association, one event per thread", "seconds": dt,
+            "hit_votes_per_s": float(sub.n_hits) * w.grid.n_phi * w.grid.n_d0 / dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1311_2769_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n_sample = max(cores, 2 * cores)
+    batch = synth.generate(w, n_events=n_sample)
+    for _ in range(args.warmup):
+        sub = batch.select(range(min(cores, n_sample)))
+        oracle.run_events(w.grid, sub.x, sub.y, sub.event_offsets, w.threshold, w.window, cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_events(w.grid, batch.x, batch.y, batch.event_offsets, w.threshold, w.window, cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n_sample / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": n_sample, "grid": [256, 32, 128],
+                       "threshold": w.threshold, "window": w.window},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": METRIC,
+                             "sample": f"events 0..{n_sample - 1} of the 4096-event batch per step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1311_2769_gb300 import build, ht, synth
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    w = synth.WORKLOADS[WORKLOAD]
+    g = w.grid
+    batch = synth.generate(w, seed=w.seed + 1000 * rank if rank else None)
+    n_events, n_hits = batch.n_events, batch.n_hits
+    cols = g.n_phi * g.n_d0
+    hit_votes = float(n_hits) * cols
+
+    ctx = ht.Context(g, w.spec.layers)
+    ctx.set_option(ht.HT_OPT_PHASE_TIMING, 1)
+    hits_d = ht.Hits.from_batch(batch, device=dev)
+    # autotune the vote tile on a 256-event sample (outside the timed region)
+    sample = batch.select(range(0, n_events, max(1, n_events // 256)))
+    ctx.autotune(ht.Hits.from_batch(sample, device=dev))
+    tile = {"tile_phi": ctx.get_option(ht.HT_OPT_TILE_PHI), "tile_d0": ctx.get_option(ht.HT_OPT_TILE_D0),
+            "threads": ctx.get_option(ht.HT_OPT_THREADS)}
+
+    # size outputs from one untimed pass
+    probe = ht.Results(1 << 20, 1 << 20, device=dev)
+    ctx.process(hits_d, w.threshold, w.window, probe)
+    try:
+        ctx.sync()
+    except ht.HtError as e:
+        if e.status != ht.HT_ERR_OVERFLOW:
+            raise
+    n_peaks, n_pairs = (int(v) for v in probe.counts.cpu().numpy())
+    del probe
+    res = ht.Results(int(n_peaks * 1.05) + 1024, int(n_pairs * 1.05) + 4096, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.process(hits_d, w.threshold, w.window, res, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ctx.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, vote_ms, rest_ms = [], [], []
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            ctx.sync()
+            step_ms.append(e0.elapsed_time(e1))
+            v, r, _ = ctx.phase_times()
+            vote_ms.append(v)
+            rest_ms.append(r)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = ctx.get_option(ht.HT_OPT_LAUNCHES)
+    counts = res.counts.cpu().numpy()
+
+    # ---- plain form (one launch sequence per event) on a 512-event sample
+    plain_ctx = ht.Context(g, w.spec.layers)
+    for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
+                 (ht.HT_OPT_THREADS, tile["threads"]), (ht.HT_OPT_MODE, ht.HT_MODE_PLAIN)):
+        plain_ctx.set_option(k, v)
+    psub = batch.select(range(0, n_events, 8))
+    ph = ht.Hits.from_batch(psub, device=dev)
+    pres = ht.Results(int(n_peaks * 0.2) + 4096, int(n_pairs * 0.2) + 65536, device=dev)
+    plain_ctx.process(ph, w.threshold, w.window, pres, stream)
+    plain_ctx.sync(allow_overflow=True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    p0.record(stream)
+    plain_ctx.process(ph, w.threshold, w.window, pres, stream)
+    p1.record(stream)
+    plain_ctx.sync(allow_overflow=True)
+    plain_eps = psub.n_events / (p0.elapsed_time(p1) / 1e3)
+    plain_ctx.close()
+
+    # ---- end to end through the C ABI: pinned host inputs and outputs
+    if True:  # every rank measures its own end-to-end rate
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hx, hy, ho, hl = pin(batch.x), pin(batch.y), pin(batch.event_offsets), pin(batch.layer)
+        hits_h = ht.Hits.__new__(ht.Hits)
+        hits_h.arrays = (hx, hy, ho, hl)
+        hits_h.struct = ht.HtHits(hx.data_ptr(), hy.data_ptr(), None, hl.data_ptr(), ho.data_ptr(), n_events,
+                                  ht.HT_HOST, n_hits)
+        rh = ht.Results.__new__(ht.Results)
+        rh.peak_cap, rh.pair_cap = res.peak_cap, res.pair_cap
+        rh.peaks = torch.empty((rh.peak_cap, 5), dtype=torch.int32).pin_memory()
+        rh.peak_offsets = torch.empty(rh.peak_cap + 1, dtype=torch.int64).pin_memory()
+        rh.hit_idx = torch.empty(rh.pair_cap, dtype=torch.int32).pin_memory()
+        rh.counts = torch.zeros(2, dtype=torch.int64).pin_memory()
+        rh.struct = ht.HtResults(rh.peaks.data_ptr(), rh.peak_cap, rh.peak_offsets.data_ptr(),
+                                 rh.hit_idx.data_ptr(), rh.pair_cap, rh.counts.data_ptr(), ht.HT_HOST)
+        ectx = ht.Context(g, w.spec.layers)
+        for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
+                     (ht.HT_OPT_THREADS, tile["threads"])):
+            ectx.set_option(k, v)
+        ectx.process(hits_h, w.threshold, w.window, rh, stream)  # warm (graph capture, buffers)
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ectx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
+            et.append(time.perf_counter() - t0)
+        ectx.close()
+        c = rh.counts.numpy()
+        h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
+        d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
+        e2e = {"value": world * n_events / float(np.mean(et)), "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et))}
+
+    # ---- roofline of the dominant kernel (vote): issue-bound ALU work
+    peaks, peak_src = _peaks()
+    clk = clocks.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    vote_s = float(np.mean(vote_ms)) / 1e3
+    ops_per_cell = 6  # add, fma, reciprocal, multiply, fma, bin test: the formula's minimum per cell
+    cells_per_launch = hit_votes
+    achieved = ops_per_cell * cells_per_launch / vote_s / 1e12
+    peak_tops = sms * 128 * sm_mhz * 1e6 / 1e12
+    acc_bytes = 4.0 * g.n_phi * g.n_d0 * g.n_kappa * n_events
+    line = {
+        "metric": METRIC, "value": world * n_events / (ms / 1e3), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_step": n_events, "hits_per_step": n_hits,
+                   "grid": [g.n_phi, g.n_d0, g.n_kappa], "threshold": w.threshold, "window": w.window,
+                   "mode": "batched persistent + CUDA graph", "l2": "flushed between timed steps",
+                   "parallelism": f"events sharded, {world} independent rank(s)", **tile},
+        "hit_votes_per_s": world * hit_votes / (ms / 1e3),
+        "peaks_per_step": int(counts[0]), "pairs_per_step": int(counts[1]),
+        "plain_events_per_s": plain_eps,
+        "batched_over_plain": (n_events / (ms / 1e3)) / plain_eps,
+        "phase_ms": {"vote": float(np.mean(vote_ms)), "peaks_assoc": float(np.mean(rest_ms))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "kernel": "vote_kernel", "ops_per_cell": ops_per_cell,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"},
+        "hbm": {"step_bytes_min": 2 * acc_bytes + 8.0 * n_hits,
+                "achieved_gbs": (2 * acc_bytes + 8.0 * n_hits) / (ms / 1e3) / 1e9,
+                "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src},
+        "clocks": clk,
+        "gpu_launches": int(launches) * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, batch)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,213 @@
+/*
+ * ht.h — C ABI of the GB300 Hough-transform track finder (libht.so).
+ *
+ * Method: Lujan et al., "GPU Enhancement of the Trigger to Extend Physics
+ * Reach at the LHC" (arXiv:1311.2769), Section 3.  Every parameter instance
+ * starts with zero votes, each hit adds one vote to every instance that
+ * contains it, local maxima of the vote array are track candidates, and the
+ * candidates' hits are collected for a confirmation fit.  Instances are the
+ * cells of a (phi0, d0, kappa) perigee-helix grid (the curved, displaced
+ * three-parameter model Section 3 calls for).  Section 4 notes that each
+ * hit's parameter-space computation is independent of all other hits, which
+ * is the parallelism this library maps onto the GPU.
+ *
+ * Geometry of a cell column (phi0_i, d0_j): n = (-sin phi0, cos phi0),
+ * q = h . n = y cos phi0 - x sin phi0, and the circle through the hit with
+ * that perigee has curvature kappa = 2 (q - d0) / (r^2 + d0^2 - 2 d0 q).
+ * The hit votes into kappa bin floor(w), w = (kappa - kappa_min) * n_kappa /
+ * (kappa_max - kappa_min), when the denominator is positive and
+ * 0 <= w < n_kappa.  The bin is defined by binary64 IEEE arithmetic on the
+ * float32 hit coordinates and float32 bin-centre tables (cos/sin phi0_i,
+ * d0_j); the library reproduces that definition bit for bit (it evaluates in
+ * float32 with a certified error bound and falls back to higher precision
+ * only when the bound cannot decide the bin).
+ *
+ * Conventions for every function:
+ *   - returns HT_OK (0) or a negative HT_ERR_* status; ht_strerror() names it
+ *     and ht_last_error() returns a message for the context's last failure;
+ *   - the caller owns every buffer it passes; device pointers are borrowed
+ *     for the duration of the call or, for asynchronous calls, until the
+ *     stream reaches the work (call ht_sync or synchronise the stream);
+ *   - a context is not thread-safe: one host thread at a time;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef HT_H
+#define HT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HT_OK 0
+#define HT_ERR_INVALID_ARG (-1) /* bad pointer, size, grid, NaN/Inf coordinate, layer id, offsets */
+#define HT_ERR_OOM (-2)         /* device or pinned allocation failed */
+#define HT_ERR_OVERFLOW (-3)    /* an output cap was hit; the true count is still returned */
+#define HT_ERR_CUDA (-4)        /* a CUDA runtime call failed (see ht_last_error) */
+#define HT_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define HT_ERR_BUDGET (-6)      /* the work does not fit the accumulator memory budget */
+#define HT_ERR_STATE (-7)       /* call out of order (e.g. ht_peaks before ht_vote) */
+
+/* ---- memory kinds ---- */
+#define HT_HOST 0
+#define HT_DEVICE 1
+
+typedef struct ht_ctx ht_ctx;
+
+/* Barrel layers: n_layers radii in cm (host memory, copied at ht_create).
+ * Used to validate hit layer ids; the vote itself uses only (x, y). */
+typedef struct {
+    int32_t n_layers;
+    const float *layer_r;
+} ht_geometry;
+
+/* Accumulator binning.  phi0 covers [0, 2 pi) in n_phi bins (bin centres
+ * (i + 1/2) 2 pi / n_phi); d0 in [d0_min, d0_max) cm and kappa in
+ * [kappa_min, kappa_max) 1/cm are split into n_d0 and n_kappa equal bins.
+ * Limits: 1 <= n_phi, n_d0 <= 65535; 1 <= n_kappa <= 4096;
+ * n_d0 * n_kappa <= 2^24; d0_min < d0_max; kappa_min < kappa_max. */
+typedef struct {
+    int32_t n_phi, n_d0, n_kappa;
+    float d0_min, d0_max, kappa_min, kappa_max;
+} ht_grid;
+
+/* Ragged-packed SoA hits of n_events events: event e owns hits
+ * [event_offsets[e], event_offsets[e+1]).  event_offsets has n_events + 1
+ * entries, starts at 0, is non-decreasing and ends at n_hits.  x, y, z in cm
+ * (finite, |x|, |y| <= 1e4), layer in [0, n_layers).  All six pointers are in
+ * the memory named by `mem` (HT_HOST or HT_DEVICE).  z may be NULL (it is
+ * carried for the caller, not used by the vote).  Host inputs are validated
+ * on the host before any launch; device inputs are validated by a kernel and
+ * an invalid batch is reported by the next synchronising call. */
+typedef struct {
+    const float *x, *y, *z;
+    const int8_t *layer;
+    const int32_t *event_offsets;
+    int32_t n_events;
+    int32_t mem;
+    int64_t n_hits;
+} ht_hits;
+
+/* One track candidate: event index within the batch, cell indices, votes. */
+typedef struct {
+    int32_t event, i_phi, i_d0, i_kappa;
+    uint32_t votes;
+} ht_peak;
+
+/* Output buffers of ht_process, all in the memory named by `mem`.
+ * peaks[peak_cap]; peak_offsets[peak_cap + 1] (CSR row pointers into hit_idx);
+ * hit_idx[pair_cap] (global hit indices of the batch, ascending within each
+ * peak); counts[2] = {n_peaks, n_pairs}, the true totals even on overflow.
+ * Peaks beyond peak_cap and pairs beyond pair_cap are dropped and the call
+ * reports HT_ERR_OVERFLOW (at ht_sync for device outputs). */
+typedef struct {
+    ht_peak *peaks;
+    int64_t peak_cap;
+    int64_t *peak_offsets;
+    int32_t *hit_idx;
+    int64_t pair_cap;
+    int64_t *counts;
+    int32_t mem;
+} ht_results;
+
+/* ---- options (ht_set_option / ht_get_option) ---- */
+#define HT_OPT_MODE 1              /* HT_MODE_BATCHED (default) or HT_MODE_PLAIN */
+#define HT_OPT_TILE_PHI 2          /* phi0 rows per vote tile: 1, 2, 4 or 8 (0 = auto) */
+#define HT_OPT_TILE_D0 3           /* d0 columns per vote tile, 1..n_d0 (0 = auto) */
+#define HT_OPT_THREADS 4           /* threads per vote CTA: 128, 256, 512 (0 = auto) */
+#define HT_OPT_ACC_BUDGET 5        /* accumulator memory budget in bytes (0 = 40 GB) */
+#define HT_OPT_COUNT_STAGES 6      /* 1 = count precision-stage usage (ht_filter_stats) */
+#define HT_OPT_USE_GRAPH 7         /* 1 = replay the batched step as a CUDA graph (default 1) */
+#define HT_OPT_PHASE_TIMING 8      /* 1 = time vote / peaks+association with device events */
+#define HT_OPT_LAUNCHES 9          /* read-only: kernels launched by the last ht_process */
+
+#define HT_MODE_BATCHED 0 /* one persistent launch per kernel over all (event, tile) items */
+#define HT_MODE_PLAIN 1   /* one launch sequence per event */
+
+/* Create a context for one geometry and grid.  Builds the bin-centre tables
+ * (float32 cos/sin of phi0_i, d0_j) and the float32-filter constants on the
+ * current CUDA device.  *out receives the context; HT_ERR_INVALID_ARG for a
+ * grid outside the limits above. */
+int ht_create(const ht_geometry *geometry, const ht_grid *grid, ht_ctx **out);
+
+/* Release every device/pinned buffer, graph and stream the context owns. */
+int ht_destroy(ht_ctx *ctx);
+
+int ht_set_option(ht_ctx *ctx, int32_t key, int64_t value);
+int ht_get_option(ht_ctx *ctx, int32_t key, int64_t *value);
+
+/* Section 3 voting: fill one accumulator per event, uint32
+ * [n_phi][n_d0][n_kappa] (kappa fastest), owned by the context.  Asynchronous
+ * on `stream`; host hits are validated and staged first.  HT_ERR_BUDGET when
+ * n_events accumulators exceed HT_OPT_ACC_BUDGET (use ht_process, which runs
+ * in waves).  The accumulators stay valid until the next ht_vote/ht_process. */
+int ht_vote(ht_ctx *ctx, const ht_hits *hits, void *stream);
+
+/* Section 3 "local maxima": cells with votes >= threshold that are strictly
+ * greater than every neighbour preceding them in linear (phi0, d0, kappa)
+ * order and >= every neighbour following them; neighbours are the distinct
+ * other cells at offsets {-1,0,1}^3, phi0 periodic, d0/kappa not.  Writes at
+ * most `cap` peaks to host memory `out`, ascending (event, linear index), and
+ * the true count to *n_out (HT_ERR_OVERFLOW if it exceeds cap).  Synchronous.
+ * The full peak list is kept on the device for ht_associate. */
+int ht_peaks(ht_ctx *ctx, uint32_t threshold, ht_peak *out, int64_t cap, int64_t *n_out);
+
+/* Hit-to-candidate association for the peaks of the last ht_peaks: hit h of
+ * a peak's event belongs to peak (i, j, k) when it votes in column (i, j) into
+ * a bin within `window` of k.  CSR into host memory: peak_offsets[n_peaks + 1]
+ * (caller sizes it from ht_peaks' count) and hit_idx[cap] (global hit indices,
+ * ascending within each peak); *n_pairs = true total (HT_ERR_OVERFLOW if it
+ * exceeds cap).  Synchronous. */
+int ht_associate(ht_ctx *ctx, int32_t window, int64_t *peak_offsets, int32_t *hit_idx,
+                 int64_t cap, int64_t *n_pairs);
+
+/* The whole path — vote, peaks, association — for a batch, in waves that
+ * respect HT_OPT_ACC_BUDGET.  With device results the call is asynchronous
+ * on `stream` (status of the device-side checks and overflow at ht_sync);
+ * with host results it synchronises before returning. */
+int ht_process(ht_ctx *ctx, const ht_hits *hits, uint32_t threshold, int32_t window,
+               const ht_results *results, void *stream);
+
+/* Copy event `event`'s accumulator from the last ht_vote to host memory
+ * `out` (n_phi * n_d0 * n_kappa uint32).  Synchronous. */
+int ht_get_accumulator(ht_ctx *ctx, int32_t event, uint32_t *out);
+
+/* Copy the bin-centre tables to host memory (any pointer may be NULL):
+ * cos_phi[n_phi], sin_phi[n_phi], d0[n_d0]. */
+int ht_get_tables(ht_ctx *ctx, float *cos_phi, float *sin_phi, float *d0);
+
+/* Wait for the context's outstanding work; returns the first deferred error
+ * (device-side validation, overflow of device outputs, CUDA errors). */
+int ht_sync(ht_ctx *ctx);
+
+/* Time the vote for a few tile shapes on `hits` and keep the fastest
+ * (HT_OPT_TILE_PHI / HT_OPT_TILE_D0 / HT_OPT_THREADS).  Synchronous. */
+int ht_autotune(ht_ctx *ctx, const ht_hits *hits, void *stream);
+
+/* Device time of the last single-wave ht_process (needs HT_OPT_PHASE_TIMING=1,
+ * read after ht_sync): ms[0] vote kernel, ms[1] peaks + association, ms[2]
+ * whole device step.  Events are recorded on the step's stream, so the
+ * numbers hold inside a replayed CUDA graph too. */
+int ht_phase_times(ht_ctx *ctx, float *ms);
+
+/* Precision-stage counters since the last reset (needs HT_OPT_COUNT_STAGES=1):
+ * out[0] cells evaluated, out[1] cells decided by the double-float stage,
+ * out[2] cells decided in binary64.  reset != 0 zeroes them after reading. */
+int ht_filter_stats(ht_ctx *ctx, int64_t *out, int32_t reset);
+
+/* Diagnostic (no paper counterpart): accuracy of the float32 reciprocal
+ * approximation the stage-1 bound relies on, over `count` consecutive float
+ * bit patterns starting at first_bits (positive normal floats).
+ * out[0] = max |rcp(x) * x - 1| scaled by 2^40, out[1] = patterns checked.
+ * Synchronous; allocates 16 bytes of device memory. */
+int ht_check_rcp(uint32_t first_bits, uint32_t count, uint64_t *out);
+
+const char *ht_strerror(int status);
+const char *ht_last_error(ht_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

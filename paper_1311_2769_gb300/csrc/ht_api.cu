@@ -1,0 +1,1051 @@
+// ht_api.cu — host side of libht.so: contexts, validation, staging, waves,
+// CUDA-graph replay of the batched step, autotuning, and the C ABI of ht.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ht_internal.h"
+
+using namespace ht;
+
+namespace {
+
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    // Grow to at least `want` elements (contents are not preserved).  Bumps *gen
+    // on reallocation so captured graphs that hold the old pointer are dropped.
+    cudaError_t ensure(size_t want, int* gen) {
+        if (want <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        size_t alloc = want + want / 4 + 16;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), alloc * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return e;
+        }
+        n = alloc;
+        if (gen) ++*gen;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct GraphKey {
+    const void* ptrs[8];
+    int64_t vals[12];
+    bool operator==(const GraphKey& o) const {
+        return std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && std::memcmp(vals, o.vals, sizeof(vals)) == 0;
+    }
+};
+
+constexpr int64_t kDefaultBudget = 40LL << 30;
+
+}  // namespace
+
+struct ht_ctx {
+    int device = 0;
+    int sms = 152;
+    ht_grid grid{};
+    int n_layers = 0;
+    KConsts K{};
+    std::vector<float> h_cphi, h_sphi, h_d0;
+    float* d_cphi = nullptr;
+    float* d_sphi = nullptr;
+    float4* d_dtab = nullptr;
+    int64_t cells = 0;
+    int64_t cols_per_event = 0;
+    int nkw = 0;
+
+    // options
+    int mode = HT_MODE_BATCHED;
+    int tile_phi = 0, tile_d = 0, threads = 0;
+    int64_t budget = kDefaultBudget;
+    bool count_stages = false;
+    bool use_graph = true;
+
+    // resolved tile configuration
+    int r_tile_phi = 1, r_tile_d = 1, r_threads = 256, r_smem = 0, r_blocks_per_sm = 1;
+
+    int gen = 0;  // buffer generation (graph invalidation)
+    DBuf<float> sx, sy;
+    DBuf<int8_t> slayer;
+    DBuf<int32_t> soffs;
+    DBuf<uint32_t> acc;
+    DBuf<uint32_t> mask;
+    DBuf<uint16_t> wpre;
+    DBuf<int32_t> npk;
+    DBuf<int64_t> colbase;
+    DBuf<int32_t> order;
+    DBuf<int32_t> paircnt;  // doubles as the association cursor after the pair scan
+    DBuf<ht_peak> peaks;
+    DBuf<int64_t> peakoff;
+    DBuf<int32_t> hitidx;
+    DBuf<int64_t> scratch;
+    int64_t* d_scal = nullptr;  // [0] peak total [1] pair total [2] wave peak base [3] wave pair base [4] extra pairs
+    int32_t* d_err = nullptr;   // validation bits
+    int32_t* d_queue = nullptr; // persistent vote queue
+    unsigned long long* d_stats = nullptr;
+    int64_t* h_pinned = nullptr;  // pinned mirror of a few scalars
+
+    // current batch (device pointers)
+    const float* cx = nullptr;
+    const float* cy = nullptr;
+    const int32_t* coffs = nullptr;
+    int64_t c_hits = 0;
+    int32_t c_events = 0;
+    int32_t c_event0 = 0;  // first event of the accumulators held (ht_vote: 0)
+    int32_t c_wave_events = 0;
+    bool have_votes = false, have_peaks = false;
+    int64_t n_peaks_held = 0;
+    uint32_t last_threshold = 0;
+
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // used when the caller passes the legacy NULL stream
+    bool pending_check = false;
+    const ht_results* pending_res = nullptr;
+    ht_results pending_copy{};
+
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    bool gvalid = false;
+
+    // optional per-phase device timing (external events, also inside graphs)
+    bool timing = false;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    float phase_ms[3] = {0, 0, 0};
+    int64_t launches = 0;  // kernels issued by the last ht_process
+
+    std::string last_error;
+};
+
+namespace {
+
+int fail(ht_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HT_ERR_OOM : HT_ERR_CUDA,  \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                 \
+    } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+// Bin-centre tables (Section 3 parameter grid): phi0_i = (i + 1/2) 2 pi / n_phi,
+// d0_j = d0_min + (j + 1/2)(d0_max - d0_min) / n_d0, rounded to float once.
+void build_tables(const ht_grid& g, std::vector<float>& c, std::vector<float>& s, std::vector<float>& d) {
+    c.resize(g.n_phi);
+    s.resize(g.n_phi);
+    d.resize(g.n_d0);
+    const double dphi = 2.0 * kPi / (double)g.n_phi;
+    for (int i = 0; i < g.n_phi; ++i) {
+        const double phi = ((double)i + 0.5) * dphi;
+        c[i] = (float)std::cos(phi);
+        s[i] = (float)std::sin(phi);
+    }
+    const double wd = ((double)g.d0_max - (double)g.d0_min) / (double)g.n_d0;
+    for (int j = 0; j < g.n_d0; ++j) d[j] = (float)((double)g.d0_min + ((double)j + 0.5) * wd);
+}
+
+// Constants of the three-stage bin evaluation (see ht_kbin.cuh for the bounds).
+KConsts make_consts(const ht_grid& g, const std::vector<float>& d0) {
+    KConsts K{};
+    const double u = std::ldexp(1.0, -24), er = std::ldexp(1.0, -22);
+    const int nk = g.n_kappa;
+    K.nphi = g.n_phi;
+    K.nd = g.n_d0;
+    K.nk = nk;
+    const double scale = (double)nk / ((double)g.kappa_max - (double)g.kappa_min);
+    const double Hd = -(double)g.kappa_min * scale;
+    K.kmin = (double)g.kappa_min;
+    K.scale = scale;
+    K.S2 = (float)(2.0 * scale);
+    K.H = (float)Hd;
+    double dabs = 0.0;
+    for (float v : d0) dabs = std::max(dabs, (double)std::fabs(v));
+    K.dabs = (float)dabs;
+    const double V0 = std::max(std::fabs(Hd), std::fabs((double)nk - Hd));
+    const double ev = er + 4.0 * u + 1.0 / 63.0;
+    const double m = std::ceil(2.0 * (ev * ((double)nk + std::fabs(Hd)) + 0.26) / (1.0 - ev)) + 1.0;
+    const double Vmax = V0 + m;
+    K.wlo = (float)(-m);
+    K.whi = (float)((double)nk + m);
+    const double S2 = (double)K.S2;
+    K.T0 = (float)(2.0 * ((er + 3.0 * u) * Vmax + u * (std::fabs(Hd) + 2.0 * ((double)nk + m)) + u));
+    K.cG1 = (float)(2.0 * (64.0 / 63.0) * 4.03 * u * Vmax * (1.0 + er) * (1.0 + er + 4.0 * u));
+    K.cG2 = (float)(2.0 * 1.01 * S2 * u * (1.0 + er));
+    K.cD1 = (float)(64.0 * 4.03 * u);
+    K.cD2 = (float)(4.1 * 1.01 * S2 * u * (1.0 + er));
+    // stage 2
+    const double two_scale = 2.0 * scale;
+    K.S2hi = (float)two_scale;
+    K.S2lo = (float)(two_scale - (double)K.S2hi);
+    K.Hhi = (float)Hd;
+    K.Hlo = (float)(Hd - (double)K.Hhi);
+    const double V2 = V0 + 2.0;
+    K.T0b = (float)(std::ldexp(1.0, -34) * (V2 + (double)nk + std::fabs(Hd)));
+    K.cGb1 = (float)(64.0 * u * u * V2);
+    K.cGb2 = (float)(20.0 * u * u * S2);
+    K.cDb = (float)std::ldexp(1.0, -23);
+    return K;
+}
+
+bool grid_ok(const ht_grid& g) {
+    if (g.n_phi < 1 || g.n_phi > 65535 || g.n_d0 < 1 || g.n_d0 > 65535) return false;
+    if (g.n_kappa < 1 || g.n_kappa > 4096) return false;
+    if ((int64_t)g.n_d0 * g.n_kappa > (1 << 24)) return false;
+    if (!std::isfinite(g.d0_min) || !std::isfinite(g.d0_max) || !(g.d0_min < g.d0_max)) return false;
+    if (!std::isfinite(g.kappa_min) || !std::isfinite(g.kappa_max) || !(g.kappa_min < g.kappa_max)) return false;
+    if (std::fabs(g.d0_min) > 1.0e4f || std::fabs(g.d0_max) > 1.0e4f) return false;
+    const double scale = (double)g.n_kappa / ((double)g.kappa_max - (double)g.kappa_min);
+    if (!(scale < 1.0e30) || std::fabs(-(double)g.kappa_min * scale) > 1.0e6) return false;
+    return true;
+}
+
+// Resolve the vote tile shape: explicit options win, otherwise ~64 KB of
+// shared accumulator per CTA (three CTAs per SM).
+int resolve_tiles(ht_ctx* ctx) {
+    const int nk = ctx->grid.n_kappa, nd = ctx->grid.n_d0;
+    int td = ctx->tile_d > 0 ? std::min(ctx->tile_d, nd) : std::min(nd, std::max(1, 65536 / (4 * nk)));
+    int tp = ctx->tile_phi;
+    if (tp <= 0) {
+        tp = 1;
+        for (int c : {8, 4, 2})
+            if ((int64_t)c * td * nk * 4 <= 65536 && c <= ctx->grid.n_phi) {
+                tp = c;
+                break;
+            }
+    }
+    int thr = ctx->threads > 0 ? ctx->threads : 256;
+    const int smem = vote_smem_bytes(tp, td, nk);
+    if (smem > 227 * 1024)
+        return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d needs %d B of shared memory", tp, td, nk, smem);
+    CU(vote_prepare(tp, smem));
+    int per_sm = 0;
+    CU(vote_occupancy(tp, thr, smem, &per_sm));
+    if (per_sm < 1) return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d with %d threads cannot launch", tp, td, nk, thr);
+    ctx->r_tile_phi = tp;
+    ctx->r_tile_d = td;
+    ctx->r_threads = thr;
+    ctx->r_smem = smem;
+    ctx->r_blocks_per_sm = per_sm;
+    return HT_OK;
+}
+
+int check_hits(ht_ctx* ctx, const ht_hits* h) {
+    if (!h) return fail(ctx, HT_ERR_INVALID_ARG, "hits is NULL");
+    if (h->mem != HT_HOST && h->mem != HT_DEVICE) return fail(ctx, HT_ERR_INVALID_ARG, "hits.mem must be HT_HOST or HT_DEVICE");
+    if (h->n_events < 0) return fail(ctx, HT_ERR_INVALID_ARG, "n_events < 0");
+    if (h->n_hits < 0 || h->n_hits > INT32_MAX) return fail(ctx, HT_ERR_INVALID_ARG, "n_hits out of range");
+    if (!h->event_offsets) return fail(ctx, HT_ERR_INVALID_ARG, "event_offsets is NULL");
+    if (h->n_hits > 0 && (!h->x || !h->y)) return fail(ctx, HT_ERR_INVALID_ARG, "x/y is NULL");
+    if (h->n_hits > 0 && ctx->n_layers > 0 && !h->layer) return fail(ctx, HT_ERR_INVALID_ARG, "layer is NULL");
+    if (h->mem == HT_HOST) {
+        const int32_t* o = h->event_offsets;
+        if (o[0] != 0 || (int64_t)o[h->n_events] != h->n_hits)
+            return fail(ctx, HT_ERR_INVALID_ARG, "event_offsets must start at 0 and end at n_hits");
+        for (int32_t e = 0; e < h->n_events; ++e)
+            if (o[e] > o[e + 1]) return fail(ctx, HT_ERR_INVALID_ARG, "event_offsets decrease at event %d", e);
+    }
+    return HT_OK;
+}
+
+// Make the batch device-resident (host inputs are copied into context buffers)
+// and queue its device-side validation.
+int stage_hits(ht_ctx* ctx, const ht_hits* h, cudaStream_t s) {
+    int st = check_hits(ctx, h);
+    if (st) return st;
+    const int64_t n = h->n_hits;
+    const int32_t ne = h->n_events;
+    if (h->mem == HT_HOST) {
+        CU(ctx->sx.ensure(std::max<int64_t>(n, 1), &ctx->gen));
+        CU(ctx->sy.ensure(std::max<int64_t>(n, 1), &ctx->gen));
+        CU(ctx->soffs.ensure(ne + 1, &ctx->gen));
+        if (n) {
+            CU(cudaMemcpyAsync(ctx->sx.p, h->x, n * sizeof(float), cudaMemcpyHostToDevice, s));
+            CU(cudaMemcpyAsync(ctx->sy.p, h->y, n * sizeof(float), cudaMemcpyHostToDevice, s));
+        }
+        CU(cudaMemcpyAsync(ctx->soffs.p, h->event_offsets, (ne + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        const int8_t* lay = nullptr;
+        if (h->layer && n) {
+            CU(ctx->slayer.ensure(n, &ctx->gen));
+            CU(cudaMemcpyAsync(ctx->slayer.p, h->layer, n, cudaMemcpyHostToDevice, s));
+            lay = ctx->slayer.p;
+        }
+        ctx->cx = ctx->sx.p;
+        ctx->cy = ctx->sy.p;
+        ctx->coffs = ctx->soffs.p;
+        if (n) CU(launch_validate(ctx->cx, ctx->cy, lay, n, ctx->coffs, ne, ctx->n_layers, ctx->d_err, s));
+    } else {
+        ctx->cx = h->x;
+        ctx->cy = h->y;
+        ctx->coffs = h->event_offsets;
+        CU(launch_validate(h->x, h->y, h->layer, n, h->event_offsets, ne, ctx->n_layers, ctx->d_err, s));
+    }
+    ctx->c_hits = n;
+    ctx->c_events = ne;
+    return HT_OK;
+}
+
+int ensure_wave_buffers(ht_ctx* ctx, int32_t wave_events) {
+    const int64_t ncols = (int64_t)wave_events * ctx->cols_per_event;
+    CU(ctx->acc.ensure(std::max<int64_t>(1, (int64_t)wave_events * ctx->cells), &ctx->gen));
+    CU(ctx->mask.ensure(std::max<int64_t>(1, ncols * ctx->nkw), &ctx->gen));
+    CU(ctx->wpre.ensure(std::max<int64_t>(1, ncols * ctx->nkw), &ctx->gen));
+    CU(ctx->npk.ensure(std::max<int64_t>(1, ncols), &ctx->gen));
+    CU(ctx->colbase.ensure(std::max<int64_t>(1, ncols + 1), &ctx->gen));
+    CU(ctx->order.ensure(std::max<int32_t>(1, wave_events), &ctx->gen));
+    CU(ctx->scratch.ensure(2 * kScanBlocks, &ctx->gen));
+    return HT_OK;
+}
+
+VoteParams vote_params(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent) {
+    VoteParams p{};
+    p.x = ctx->cx;
+    p.y = ctx->cy;
+    p.offs = ctx->coffs;
+    p.n_hits = ctx->c_hits;
+    p.event0 = event0;
+    p.n_events = ne;
+    p.order = persistent ? ctx->order.p : nullptr;
+    p.queue = persistent ? ctx->d_queue : nullptr;
+    p.item0 = 0;
+    p.tiles_phi = (ctx->grid.n_phi + ctx->r_tile_phi - 1) / ctx->r_tile_phi;
+    p.tiles_d = (ctx->grid.n_d0 + ctx->r_tile_d - 1) / ctx->r_tile_d;
+    p.tile_d = ctx->r_tile_d;
+    p.n_items = ne * p.tiles_phi * p.tiles_d;
+    p.acc = ctx->acc.p;
+    p.cells = ctx->cells;
+    p.cphi = ctx->d_cphi;
+    p.sphi = ctx->d_sphi;
+    p.dtab = ctx->d_dtab;
+    p.K = ctx->K;
+    p.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+    return p;
+}
+
+// Vote events [event0, event0 + ne) of the staged batch into acc[0..ne).
+int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStream_t s) {
+    if (ne <= 0) return HT_OK;
+    VoteParams p = vote_params(ctx, event0, ne, persistent);
+    if (persistent) {
+        CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
+        CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), s));
+        const int grid = std::min<int64_t>(p.n_items, (int64_t)ctx->sms * ctx->r_blocks_per_sm);
+        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s));
+    } else {
+        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s));
+    }
+    return HT_OK;
+}
+
+PeakParams peak_params(ht_ctx* ctx, int32_t event0, int32_t ne, uint32_t thr, ht_peak* peaks, int64_t cap,
+                       int32_t window) {
+    PeakParams p{};
+    p.acc = ctx->acc.p;
+    p.cells = ctx->cells;
+    p.n_events = ne;
+    p.event0 = event0;
+    p.thr = thr;
+    p.nphi = ctx->grid.n_phi;
+    p.nd = ctx->grid.n_d0;
+    p.nk = ctx->grid.n_kappa;
+    p.nkw = ctx->nkw;
+    p.mask = ctx->mask.p;
+    p.wpre = ctx->wpre.p;
+    p.npk = ctx->npk.p;
+    p.colbase = ctx->colbase.p;
+    p.peaks = peaks;
+    p.peak_cap = cap;
+    p.window = window;
+    p.paircnt = ctx->paircnt.p;
+    p.extra_pairs = ctx->d_scal + 4;
+    return p;
+}
+
+// detect + scan of per-column peak counts; colbase starts at d_scal[0] (running
+// peak total), which is advanced to include this wave's peaks.
+int run_detect_scan(ht_ctx* ctx, const PeakParams& pp, cudaStream_t s) {
+    CU(launch_detect(pp, s));
+    CU(cudaMemcpyAsync(ctx->d_scal + 2, ctx->d_scal + 0, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    ScanRange r{};
+    r.in = ctx->npk.p;
+    r.out = ctx->colbase.p;
+    r.lo = 0;
+    r.hi = (int64_t)pp.n_events * ctx->cols_per_event;
+    r.cap = r.hi;
+    r.base_dev = ctx->d_scal + 2;
+    r.total = ctx->d_scal + 0;
+    r.write_end = 0;
+    CU(launch_scan(r, ctx->scratch.p, s));
+    return HT_OK;
+}
+
+// pair offsets for this wave's peaks [d_scal[2], d_scal[0]) clamped to cap, and association
+int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, int64_t* peak_offsets,
+                    int32_t* hit_idx, int64_t pair_cap, int32_t window, cudaStream_t s) {
+    CU(cudaMemcpyAsync(ctx->d_scal + 3, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    ScanRange r{};
+    r.in = ctx->paircnt.p;
+    r.out = peak_offsets;
+    r.lo_dev = ctx->d_scal + 2;
+    r.hi_dev = ctx->d_scal + 0;
+    r.cap = peak_cap;
+    r.base_dev = ctx->d_scal + 3;
+    r.total = ctx->d_scal + 1;
+    r.write_end = 1;
+    CU(launch_scan(r, ctx->scratch.p, s));
+    // the pair counts are consumed: reuse the buffer as per-peak cursors
+    if (peak_cap > 0) CU(cudaMemsetAsync(ctx->paircnt.p, 0, peak_cap * sizeof(int32_t), s));
+    AssocParams a{};
+    a.x = ctx->cx;
+    a.y = ctx->cy;
+    a.offs = ctx->coffs;
+    a.n_hits = ctx->c_hits;
+    a.event0 = event0;
+    a.n_events = ne;
+    a.mask = ctx->mask.p;
+    a.wpre = ctx->wpre.p;
+    a.npk = ctx->npk.p;
+    a.colbase = ctx->colbase.p;
+    a.peak_offsets = peak_offsets;
+    a.peak_cap = peak_cap;
+    a.cursor = ctx->paircnt.p;
+    a.hit_idx = hit_idx;
+    a.pair_cap = pair_cap;
+    a.window = window;
+    a.cphi = ctx->d_cphi;
+    a.sphi = ctx->d_sphi;
+    a.dtab = ctx->d_dtab;
+    a.K = ctx->K;
+    a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+    CU(launch_assoc(a, s));
+    return HT_OK;
+}
+
+// The legacy default stream cannot be captured into a graph; a caller's NULL
+// stream is replaced by a context-owned blocking stream, which the legacy
+// stream synchronises with implicitly (both directions).
+int resolve_stream(ht_ctx* ctx, void* stream, cudaStream_t* out) {
+    if (stream) {
+        *out = (cudaStream_t)stream;
+        return HT_OK;
+    }
+    if (!ctx->own_stream) CU(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamDefault));
+    *out = ctx->own_stream;
+    return HT_OK;
+}
+
+int32_t events_per_wave(ht_ctx* ctx, int32_t n_events) {
+    const int64_t per = ctx->cells * 4;
+    int64_t w = ctx->budget / std::max<int64_t>(per, 1);
+    if (w < 1) return 0;
+    return (int32_t)std::min<int64_t>(w, std::max<int32_t>(n_events, 1));
+}
+
+// Device work of ht_process for the staged batch (graph-capturable).
+// Records one of the phase events (external, so it also works inside a graph).
+int mark(ht_ctx* ctx, int which, cudaStream_t s) {
+    if (ctx->timing) CU(cudaEventRecordWithFlags(ctx->tev[which], s, cudaEventRecordExternal));
+    return HT_OK;
+}
+
+int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, int64_t peak_cap,
+                   int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t epw, cudaStream_t s) {
+    CU(cudaMemsetAsync(ctx->d_scal, 0, 8 * sizeof(int64_t), s));
+    const bool plain = ctx->mode == HT_MODE_PLAIN;
+    const int32_t step = plain ? 1 : epw;
+    // kernels per wave: [order] vote, detect, scan x3, emit, scan x3, assoc
+    ctx->launches = 1;  // finalize
+    int st = HT_OK;
+    const bool single = ctx->c_events <= step;  // phase timing needs one wave
+    for (int32_t e0 = 0; e0 < ctx->c_events; e0 += step) {
+        const int32_t ne = std::min(step, ctx->c_events - e0);
+        if (single && (st = mark(ctx, 0, s))) return st;
+        st = run_vote(ctx, e0, ne, !plain, s);
+        if (st) return st;
+        if (single && (st = mark(ctx, 1, s))) return st;
+        PeakParams pp = peak_params(ctx, e0, ne, thr, peaks, peak_cap, window);
+        st = run_detect_scan(ctx, pp, s);
+        if (st) return st;
+        CU(launch_emit(pp, s));
+        st = run_pairs_assoc(ctx, e0, ne, peak_cap, peak_offsets, hit_idx, pair_cap, window, s);
+        if (st) return st;
+        if (single && (st = mark(ctx, 2, s))) return st;
+        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1;
+    }
+    if (single && (st = mark(ctx, 3, s))) return st;
+    if (ctx->c_events == 0 && peak_offsets && peak_cap >= 0)
+        CU(cudaMemsetAsync(peak_offsets, 0, sizeof(int64_t), s));
+    CU(launch_finalize(ctx->d_scal, s));
+    return HT_OK;
+}
+
+int read_err(ht_ctx* ctx) {
+    int32_t err = 0;
+    CU(cudaMemcpy(&err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (err) {
+        CU(cudaMemset(ctx->d_err, 0, sizeof(int32_t)));
+        return fail(ctx, HT_ERR_INVALID_ARG, "invalid hits in batch:%s%s%s", (err & 1) ? " non-finite or |coordinate|>1e4" : "",
+                    (err & 2) ? " layer id out of range" : "", (err & 4) ? " bad event offsets" : "");
+    }
+    return HT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ht_strerror(int status) {
+    switch (status) {
+        case HT_OK: return "ok";
+        case HT_ERR_INVALID_ARG: return "invalid argument";
+        case HT_ERR_OOM: return "out of memory";
+        case HT_ERR_OVERFLOW: return "output capacity exceeded";
+        case HT_ERR_CUDA: return "CUDA error";
+        case HT_ERR_TIMEOUT: return "device wait timed out";
+        case HT_ERR_BUDGET: return "accumulator memory budget exceeded";
+        case HT_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* ht_last_error(ht_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
+    ht_ctx* ctx = nullptr;
+    int dev_probe = 0;
+    if (!out || !grid) return HT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid_ok(*grid)) return HT_ERR_INVALID_ARG;
+    if (geometry && (geometry->n_layers < 0 || geometry->n_layers > 127 || (geometry->n_layers > 0 && !geometry->layer_r)))
+        return HT_ERR_INVALID_ARG;
+    if (cudaGetDevice(&dev_probe) != cudaSuccess) {
+        cudaGetLastError();
+        return HT_ERR_CUDA;
+    }
+    ctx = new ht_ctx();
+    ctx->grid = *grid;
+    ctx->n_layers = geometry ? geometry->n_layers : 0;
+    ctx->device = dev_probe;
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        delete ctx;
+        return HT_ERR_CUDA;
+    }
+    build_tables(*grid, ctx->h_cphi, ctx->h_sphi, ctx->h_d0);
+    ctx->K = make_consts(*grid, ctx->h_d0);
+    ctx->cells = (int64_t)grid->n_phi * grid->n_d0 * grid->n_kappa;
+    ctx->cols_per_event = (int64_t)grid->n_phi * grid->n_d0;
+    ctx->nkw = (grid->n_kappa + 31) / 32;
+    std::vector<float4> dt(grid->n_d0);
+    for (int j = 0; j < grid->n_d0; ++j) {
+        const float d = ctx->h_d0[j];
+        dt[j] = make_float4(d, d + d, d * d, 0.0f);
+    }
+    int st = HT_OK;
+    auto bad = [&](cudaError_t e) {
+        if (e == cudaSuccess) return false;
+        st = fail(ctx, e == cudaErrorMemoryAllocation ? HT_ERR_OOM : HT_ERR_CUDA, "ht_create: %s", cudaGetErrorString(e));
+        return true;
+    };
+    if (bad(cudaMalloc(&ctx->d_cphi, grid->n_phi * sizeof(float))) ||
+        bad(cudaMalloc(&ctx->d_sphi, grid->n_phi * sizeof(float))) ||
+        bad(cudaMalloc(&ctx->d_dtab, grid->n_d0 * sizeof(float4))) ||
+        bad(cudaMalloc(&ctx->d_scal, 8 * sizeof(int64_t))) || bad(cudaMalloc(&ctx->d_err, sizeof(int32_t))) ||
+        bad(cudaMalloc(&ctx->d_queue, sizeof(int32_t))) || bad(cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long))) ||
+        bad(cudaMallocHost(&ctx->h_pinned, 8 * sizeof(int64_t))) ||
+        bad(cudaMemcpy(ctx->d_cphi, ctx->h_cphi.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemcpy(ctx->d_sphi, ctx->h_sphi.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemcpy(ctx->d_dtab, dt.data(), grid->n_d0 * sizeof(float4), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemset(ctx->d_err, 0, sizeof(int32_t))) || bad(cudaMemset(ctx->d_stats, 0, 4 * sizeof(unsigned long long))) ||
+        bad(cudaMemset(ctx->d_scal, 0, 8 * sizeof(int64_t)))) {
+        ht_destroy(ctx);
+        return st;
+    }
+    st = resolve_tiles(ctx);
+    if (st) {
+        ht_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return HT_OK;
+}
+
+int ht_destroy(ht_ctx* ctx) {
+    if (!ctx) return HT_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (auto& e : ctx->tev)
+        if (e) cudaEventDestroy(e);
+    for (void* p : {(void*)ctx->d_cphi, (void*)ctx->d_sphi, (void*)ctx->d_dtab, (void*)ctx->d_scal, (void*)ctx->d_err,
+                    (void*)ctx->d_queue, (void*)ctx->d_stats})
+        if (p) cudaFree(p);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    ctx->sx.release();
+    ctx->sy.release();
+    ctx->slayer.release();
+    ctx->soffs.release();
+    ctx->acc.release();
+    ctx->mask.release();
+    ctx->wpre.release();
+    ctx->npk.release();
+    ctx->colbase.release();
+    ctx->order.release();
+    ctx->paircnt.release();
+    ctx->peaks.release();
+    ctx->peakoff.release();
+    ctx->hitidx.release();
+    ctx->scratch.release();
+    delete ctx;
+    return HT_OK;
+}
+
+int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
+    if (!ctx) return HT_ERR_INVALID_ARG;
+    switch (key) {
+        case HT_OPT_MODE:
+            if (value != HT_MODE_BATCHED && value != HT_MODE_PLAIN) return fail(ctx, HT_ERR_INVALID_ARG, "bad mode");
+            ctx->mode = (int)value;
+            break;
+        case HT_OPT_TILE_PHI:
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+                return fail(ctx, HT_ERR_INVALID_ARG, "tile_phi must be 0, 1, 2, 4 or 8");
+            ctx->tile_phi = (int)value;
+            break;
+        case HT_OPT_TILE_D0:
+            if (value < 0 || value > ctx->grid.n_d0) return fail(ctx, HT_ERR_INVALID_ARG, "tile_d0 out of range");
+            ctx->tile_d = (int)value;
+            break;
+        case HT_OPT_THREADS:
+            if (value != 0 && value != 128 && value != 256 && value != 512)
+                return fail(ctx, HT_ERR_INVALID_ARG, "threads must be 0, 128, 256 or 512");
+            ctx->threads = (int)value;
+            break;
+        case HT_OPT_ACC_BUDGET:
+            if (value < 0) return fail(ctx, HT_ERR_INVALID_ARG, "budget < 0");
+            ctx->budget = value ? value : kDefaultBudget;
+            break;
+        case HT_OPT_COUNT_STAGES: ctx->count_stages = value != 0; break;
+        case HT_OPT_USE_GRAPH: ctx->use_graph = value != 0; break;
+        case HT_OPT_PHASE_TIMING:
+            if (value && !ctx->tev[0])
+                for (auto& e : ctx->tev) CU(cudaEventCreate(&e));
+            ctx->timing = value != 0;
+            break;
+        default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
+    }
+    ctx->gvalid = false;
+    if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS) {
+        int st = resolve_tiles(ctx);
+        if (st) return st;
+    }
+    return HT_OK;
+}
+
+int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
+    if (!ctx || !value) return HT_ERR_INVALID_ARG;
+    switch (key) {
+        case HT_OPT_MODE: *value = ctx->mode; break;
+        case HT_OPT_TILE_PHI: *value = ctx->r_tile_phi; break;
+        case HT_OPT_TILE_D0: *value = ctx->r_tile_d; break;
+        case HT_OPT_THREADS: *value = ctx->r_threads; break;
+        case HT_OPT_ACC_BUDGET: *value = ctx->budget; break;
+        case HT_OPT_COUNT_STAGES: *value = ctx->count_stages; break;
+        case HT_OPT_USE_GRAPH: *value = ctx->use_graph; break;
+        case HT_OPT_PHASE_TIMING: *value = ctx->timing; break;
+        case HT_OPT_LAUNCHES: *value = ctx->launches; break;
+        default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
+    }
+    return HT_OK;
+}
+
+int ht_vote(ht_ctx* ctx, const ht_hits* hits, void* stream) {
+    if (!ctx) return HT_ERR_INVALID_ARG;
+    cudaStream_t s = nullptr;
+    if (int st0 = resolve_stream(ctx, stream, &s)) return st0;
+    if (hits && (int64_t)hits->n_events * ctx->cells * 4 > ctx->budget)
+        return fail(ctx, HT_ERR_BUDGET, "%d accumulators of %lld B exceed the budget of %lld B", hits->n_events,
+                    (long long)(ctx->cells * 4), (long long)ctx->budget);
+    int st = stage_hits(ctx, hits, s);
+    if (st) return st;
+    ctx->stream = s;
+    ctx->have_votes = ctx->have_peaks = false;
+    st = ensure_wave_buffers(ctx, ctx->c_events);
+    if (st) return st;
+    const bool plain = ctx->mode == HT_MODE_PLAIN;
+    if (plain) {
+        for (int32_t e = 0; e < ctx->c_events; ++e) {
+            VoteParams p = vote_params(ctx, e, 1, false);
+            p.acc = ctx->acc.p + (int64_t)e * ctx->cells;
+            CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s));
+        }
+    } else {
+        st = run_vote(ctx, 0, ctx->c_events, true, s);
+        if (st) return st;
+    }
+    ctx->c_event0 = 0;
+    ctx->c_wave_events = ctx->c_events;
+    ctx->have_votes = true;
+    return HT_OK;
+}
+
+int ht_peaks(ht_ctx* ctx, uint32_t threshold, ht_peak* out, int64_t cap, int64_t* n_out) {
+    if (!ctx || !n_out || cap < 0 || (cap > 0 && !out)) return HT_ERR_INVALID_ARG;
+    if (!ctx->have_votes) return fail(ctx, HT_ERR_STATE, "ht_peaks needs a preceding ht_vote");
+    cudaStream_t s = ctx->stream;
+    int st = read_err(ctx);
+    if (st) return st;
+    CU(cudaMemsetAsync(ctx->d_scal, 0, 8 * sizeof(int64_t), s));
+    PeakParams pp = peak_params(ctx, 0, ctx->c_events, threshold, nullptr, 0, -1);
+    st = run_detect_scan(ctx, pp, s);
+    if (st) return st;
+    CU(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scal, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int64_t total = ctx->h_pinned[0];
+    CU(ctx->peaks.ensure(std::max<int64_t>(total, 1), &ctx->gen));
+    pp.peaks = ctx->peaks.p;
+    pp.peak_cap = total;
+    CU(launch_emit(pp, s));
+    const int64_t ncopy = std::min(total, cap);
+    if (ncopy > 0) CU(cudaMemcpyAsync(out, ctx->peaks.p, ncopy * sizeof(ht_peak), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *n_out = total;
+    ctx->n_peaks_held = total;
+    ctx->last_threshold = threshold;
+    ctx->have_peaks = true;
+    if (total > cap) return fail(ctx, HT_ERR_OVERFLOW, "%lld peaks, cap %lld", (long long)total, (long long)cap);
+    return HT_OK;
+}
+
+int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hit_idx, int64_t cap, int64_t* n_pairs) {
+    if (!ctx || !n_pairs || !peak_offsets || cap < 0 || (cap > 0 && !hit_idx) || window < 0 || window > 15)
+        return HT_ERR_INVALID_ARG;
+    if (!ctx->have_peaks) return fail(ctx, HT_ERR_STATE, "ht_associate needs a preceding ht_peaks");
+    cudaStream_t s = ctx->stream;
+    const int64_t np = ctx->n_peaks_held;
+    CU(ctx->paircnt.ensure(std::max<int64_t>(np, 1), &ctx->gen));
+    CU(ctx->peakoff.ensure(np + 1, &ctx->gen));
+    // per-peak pair counts from the accumulators, then their scan
+    CU(cudaMemsetAsync(ctx->d_scal, 0, 8 * sizeof(int64_t), s));
+    ctx->h_pinned[0] = np;
+    CU(cudaMemcpyAsync(ctx->d_scal + 0, ctx->h_pinned, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    PeakParams pp = peak_params(ctx, 0, ctx->c_events, ctx->last_threshold, ctx->peaks.p, np, window);
+    CU(launch_paircount(pp, ctx->d_scal + 2, ctx->d_scal + 0, s));
+    CU(cudaMemcpyAsync(ctx->d_scal + 3, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    ScanRange r{};
+    r.in = ctx->paircnt.p;
+    r.out = ctx->peakoff.p;
+    r.lo_dev = ctx->d_scal + 2;
+    r.hi_dev = ctx->d_scal + 0;
+    r.cap = np;
+    r.base_dev = ctx->d_scal + 3;
+    r.total = ctx->d_scal + 1;
+    r.write_end = 1;
+    CU(launch_scan(r, ctx->scratch.p, s));
+    CU(cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int64_t total = ctx->h_pinned[1];
+    CU(ctx->hitidx.ensure(std::max<int64_t>(total, 1), &ctx->gen));
+    if (np > 0) CU(cudaMemsetAsync(ctx->paircnt.p, 0, np * sizeof(int32_t), s));
+    AssocParams a{};
+    a.x = ctx->cx;
+    a.y = ctx->cy;
+    a.offs = ctx->coffs;
+    a.n_hits = ctx->c_hits;
+    a.event0 = 0;
+    a.n_events = ctx->c_events;
+    a.mask = ctx->mask.p;
+    a.wpre = ctx->wpre.p;
+    a.npk = ctx->npk.p;
+    a.colbase = ctx->colbase.p;
+    a.peak_offsets = ctx->peakoff.p;
+    a.peak_cap = np;
+    a.cursor = ctx->paircnt.p;
+    a.hit_idx = ctx->hitidx.p;
+    a.pair_cap = total;
+    a.window = window;
+    a.cphi = ctx->d_cphi;
+    a.sphi = ctx->d_sphi;
+    a.dtab = ctx->d_dtab;
+    a.K = ctx->K;
+    a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+    CU(launch_assoc(a, s));
+    CU(cudaMemcpyAsync(peak_offsets, ctx->peakoff.p, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    const int64_t ncopy = std::min(total, cap);
+    if (ncopy > 0) CU(cudaMemcpyAsync(hit_idx, ctx->hitidx.p, ncopy * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *n_pairs = total;
+    if (total > cap) return fail(ctx, HT_ERR_OVERFLOW, "%lld pairs, cap %lld", (long long)total, (long long)cap);
+    return HT_OK;
+}
+
+int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t window, const ht_results* res,
+               void* stream) {
+    if (!ctx || !res || window < 0 || window > 15) return HT_ERR_INVALID_ARG;
+    if (res->peak_cap < 0 || res->pair_cap < 0 || !res->counts || !res->peak_offsets ||
+        (res->peak_cap > 0 && !res->peaks) || (res->pair_cap > 0 && !res->hit_idx) ||
+        (res->mem != HT_HOST && res->mem != HT_DEVICE))
+        return fail(ctx, HT_ERR_INVALID_ARG, "bad ht_results");
+    cudaStream_t s = nullptr;
+    if (int st0 = resolve_stream(ctx, stream, &s)) return st0;
+    int st = stage_hits(ctx, hits, s);
+    if (st) return st;
+    ctx->stream = s;
+    ctx->have_votes = ctx->have_peaks = false;
+    const int32_t epw = events_per_wave(ctx, ctx->c_events);
+    if (epw < 1)
+        return fail(ctx, HT_ERR_BUDGET, "one accumulator (%lld B) exceeds the budget", (long long)(ctx->cells * 4));
+    st = ensure_wave_buffers(ctx, ctx->mode == HT_MODE_PLAIN ? 1 : epw);
+    if (st) return st;
+    const int64_t pcap = res->peak_cap, qcap = res->pair_cap;
+    CU(ctx->paircnt.ensure(std::max<int64_t>(pcap, 1), &ctx->gen));
+    ht_peak* peaks = res->peaks;
+    int64_t* poff = res->peak_offsets;
+    int32_t* hidx = res->hit_idx;
+    if (res->mem == HT_HOST) {
+        CU(ctx->peaks.ensure(std::max<int64_t>(pcap, 1), &ctx->gen));
+        CU(ctx->peakoff.ensure(pcap + 1, &ctx->gen));
+        CU(ctx->hitidx.ensure(std::max<int64_t>(qcap, 1), &ctx->gen));
+        peaks = ctx->peaks.p;
+        poff = ctx->peakoff.p;
+        hidx = ctx->hitidx.p;
+    }
+    const bool graph = ctx->use_graph && ctx->mode == HT_MODE_BATCHED;
+    if (graph) {
+        GraphKey key{};
+        key.ptrs[0] = ctx->cx;
+        key.ptrs[1] = ctx->cy;
+        key.ptrs[2] = ctx->coffs;
+        key.ptrs[3] = peaks;
+        key.ptrs[4] = poff;
+        key.ptrs[5] = hidx;
+        key.ptrs[6] = s;
+        key.vals[0] = ctx->c_hits;
+        key.vals[1] = ctx->c_events;
+        key.vals[2] = threshold;
+        key.vals[3] = window;
+        key.vals[4] = pcap;
+        key.vals[5] = qcap;
+        key.vals[6] = epw;
+        key.vals[7] = ctx->gen;
+        key.vals[8] = ctx->r_tile_phi * 100000 + ctx->r_tile_d;
+        key.vals[9] = ctx->r_threads;
+        key.vals[10] = ctx->count_stages * 2 + ctx->timing;
+        if (!ctx->gvalid || !(key == ctx->gkey)) {
+            if (ctx->gexec) {
+                cudaGraphExecDestroy(ctx->gexec);
+                ctx->gexec = nullptr;
+            }
+            ctx->gvalid = false;
+            cudaGraph_t g = nullptr;
+            CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, epw, s);
+            cudaError_t ce = cudaStreamEndCapture(s, &g);
+            if (st) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            CU(ce);
+            cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaGraphDestroy(g);
+            CU(ie);
+            ctx->gkey = key;
+            ctx->gvalid = true;
+        }
+        CU(cudaGraphLaunch(ctx->gexec, s));
+    } else {
+        st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, epw, s);
+        if (st) return st;
+    }
+    // counts = {peak total, pair total + pairs of peaks beyond the cap}
+    if (res->mem == HT_DEVICE) {
+        CU(cudaMemcpyAsync(res->counts, ctx->d_scal + 6, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        ctx->pending_check = true;
+        ctx->pending_copy = *res;
+        return HT_OK;
+    }
+    CU(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scal + 6, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    st = read_err(ctx);
+    if (st) return st;
+    const int64_t np = ctx->h_pinned[0], nq = ctx->h_pinned[1];
+    res->counts[0] = np;
+    res->counts[1] = nq;
+    const int64_t cp = std::min(np, pcap), cq = std::min(nq, qcap);
+    if (cp > 0) CU(cudaMemcpyAsync(res->peaks, peaks, cp * sizeof(ht_peak), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(res->peak_offsets, poff, (cp + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (cq > 0) CU(cudaMemcpyAsync(res->hit_idx, hidx, cq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (np > pcap || nq > qcap)
+        return fail(ctx, HT_ERR_OVERFLOW, "%lld peaks (cap %lld), %lld pairs (cap %lld)", (long long)np,
+                    (long long)pcap, (long long)nq, (long long)qcap);
+    return HT_OK;
+}
+
+int ht_sync(ht_ctx* ctx) {
+    if (!ctx) return HT_ERR_INVALID_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->timing && ctx->c_events > 0) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[1]) == cudaSuccess) ctx->phase_ms[0] = ms;
+        if (cudaEventElapsedTime(&ms, ctx->tev[1], ctx->tev[2]) == cudaSuccess) ctx->phase_ms[1] = ms;
+        if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[3]) == cudaSuccess) ctx->phase_ms[2] = ms;
+        cudaGetLastError();
+    }
+    int st = read_err(ctx);
+    if (st) return st;
+    if (ctx->pending_check) {
+        ctx->pending_check = false;
+        CU(cudaMemcpy(ctx->h_pinned, ctx->d_scal + 6, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (ctx->h_pinned[0] > ctx->pending_copy.peak_cap || ctx->h_pinned[1] > ctx->pending_copy.pair_cap)
+            return fail(ctx, HT_ERR_OVERFLOW, "%lld peaks (cap %lld), %lld pairs (cap %lld)",
+                        (long long)ctx->h_pinned[0], (long long)ctx->pending_copy.peak_cap,
+                        (long long)ctx->h_pinned[1], (long long)ctx->pending_copy.pair_cap);
+    }
+    return HT_OK;
+}
+
+int ht_get_accumulator(ht_ctx* ctx, int32_t event, uint32_t* out) {
+    if (!ctx || !out) return HT_ERR_INVALID_ARG;
+    if (!ctx->have_votes) return fail(ctx, HT_ERR_STATE, "no accumulators: call ht_vote first");
+    if (event < 0 || event >= ctx->c_wave_events) return fail(ctx, HT_ERR_INVALID_ARG, "event %d out of range", event);
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpy(out, ctx->acc.p + (int64_t)event * ctx->cells, ctx->cells * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return HT_OK;
+}
+
+int ht_get_tables(ht_ctx* ctx, float* cos_phi, float* sin_phi, float* d0) {
+    if (!ctx) return HT_ERR_INVALID_ARG;
+    if (cos_phi) std::memcpy(cos_phi, ctx->h_cphi.data(), ctx->h_cphi.size() * sizeof(float));
+    if (sin_phi) std::memcpy(sin_phi, ctx->h_sphi.data(), ctx->h_sphi.size() * sizeof(float));
+    if (d0) std::memcpy(d0, ctx->h_d0.data(), ctx->h_d0.size() * sizeof(float));
+    return HT_OK;
+}
+
+int ht_phase_times(ht_ctx* ctx, float* ms) {
+    if (!ctx || !ms) return HT_ERR_INVALID_ARG;
+    if (!ctx->timing) return fail(ctx, HT_ERR_STATE, "HT_OPT_PHASE_TIMING is off");
+    for (int i = 0; i < 3; ++i) ms[i] = ctx->phase_ms[i];
+    return HT_OK;
+}
+
+int ht_filter_stats(ht_ctx* ctx, int64_t* out, int32_t reset) {
+    if (!ctx || !out) return HT_ERR_INVALID_ARG;
+    unsigned long long v[4];
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(v, ctx->d_stats, sizeof v, cudaMemcpyDeviceToHost));
+    out[0] = (int64_t)v[0];
+    out[1] = (int64_t)v[1];
+    out[2] = (int64_t)v[2];
+    if (reset) CU(cudaMemset(ctx->d_stats, 0, sizeof v));
+    return HT_OK;
+}
+
+int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
+    if (!ctx) return HT_ERR_INVALID_ARG;
+    cudaStream_t s = nullptr;
+    if (int st0 = resolve_stream(ctx, stream, &s)) return st0;
+    const int64_t budget_ev = ctx->budget / std::max<int64_t>(ctx->cells * 4, 1);
+    if (hits && (int64_t)hits->n_events > budget_ev)
+        return fail(ctx, HT_ERR_BUDGET, "autotune sample exceeds the accumulator budget");
+    int st = stage_hits(ctx, hits, s);
+    if (st) return st;
+    ctx->stream = s;
+    st = ensure_wave_buffers(ctx, ctx->c_events);
+    if (st) return st;
+    const int nk = ctx->grid.n_kappa, nd = ctx->grid.n_d0;
+    const int save_p = ctx->tile_phi, save_d = ctx->tile_d, save_t = ctx->threads;
+    std::vector<int> tds;
+    for (int td : {nd, 128, 64, 32, 16, 8})
+        if (td <= nd && std::find(tds.begin(), tds.end(), td) == tds.end()) tds.push_back(td);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bp = 0, bd = 0, bt = 0;
+    for (int tp : {1, 2, 4, 8}) {
+        if (tp > ctx->grid.n_phi) continue;
+        for (int td : tds) {
+            const int smem = vote_smem_bytes(tp, td, nk);
+            if (smem > 200 * 1024 || smem < 8 * 1024) continue;
+            for (int thr : {256, 512}) {
+                ctx->tile_phi = tp;
+                ctx->tile_d = td;
+                ctx->threads = thr;
+                if (resolve_tiles(ctx)) continue;
+                run_vote(ctx, 0, ctx->c_events, true, s);  // warm
+                CU(cudaEventRecord(e0, s));
+                for (int r = 0; r < 2; ++r) run_vote(ctx, 0, ctx->c_events, true, s);
+                CU(cudaEventRecord(e1, s));
+                CU(cudaEventSynchronize(e1));
+                float ms = 0;
+                CU(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    bp = tp;
+                    bd = td;
+                    bt = thr;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bp == 0) {
+        ctx->tile_phi = save_p;
+        ctx->tile_d = save_d;
+        ctx->threads = save_t;
+        resolve_tiles(ctx);
+        return fail(ctx, HT_ERR_INVALID_ARG, "no tile shape fits");
+    }
+    ctx->tile_phi = bp;
+    ctx->tile_d = bd;
+    ctx->threads = bt;
+    ctx->gvalid = false;
+    ctx->have_votes = ctx->have_peaks = false;
+    return resolve_tiles(ctx);
+}
+
+// Accuracy of rcp.approx.ftz.f32 over `count` consecutive float bit patterns
+// starting at first_bits: out[0] = max |rcp(x) x - 1| * 2^40, out[1] = count.
+int ht_check_rcp(uint32_t first_bits, uint32_t count, uint64_t* out) {
+    ht_ctx* ctx = nullptr;
+    if (!out) return HT_ERR_INVALID_ARG;
+    unsigned long long* d = nullptr;
+    CU(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    CU(cudaMemset(d, 0, 2 * sizeof(unsigned long long)));
+    CU(launch_rcp_check(first_bits, count, d, nullptr));
+    CU(cudaMemcpy(out, d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    CU(cudaFree(d));
+    return HT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// ht_internal.h — kernel launch interface shared by the host API and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/ht.h"
+#include "ht_kbin.cuh"
+
+namespace ht {
+
+struct VoteParams {
+    const float* x;
+    const float* y;
+    const int32_t* offs;   // batch event offsets (n_events_batch + 1)
+    int64_t n_hits;
+    int32_t event0;        // first batch event of this wave
+    int32_t n_events;      // events in this wave
+    const int32_t* order;  // wave-local event order (LPT) or nullptr
+    int32_t* queue;        // persistent work counter (zeroed) or nullptr: one item per block
+    int32_t item0;         // first item (non-persistent launches)
+    int32_t n_items;       // items = n_events * tiles_phi * tiles_d
+    int32_t tiles_phi, tiles_d, tile_d;
+    uint32_t* acc;         // wave accumulators [n_events][cells]
+    int64_t cells;
+    const float* cphi;
+    const float* sphi;
+    const float4* dtab;    // (d0_j, 2 d0_j, d0_j^2, 0)
+    KConsts K;
+    unsigned long long* stats;
+};
+
+struct PeakParams {
+    const uint32_t* acc;
+    int64_t cells;
+    int32_t n_events;       // wave events
+    int32_t event0;         // batch index of the wave's first event
+    uint32_t thr;
+    int32_t nphi, nd, nk, nkw;
+    uint32_t* mask;         // [cols][nkw] peak bits
+    uint16_t* wpre;         // [cols][nkw] peaks in earlier words of the column
+    int32_t* npk;           // [cols]
+    int64_t* colbase;       // [cols] first peak id of the column (global, includes earlier waves)
+    ht_peak* peaks;
+    int64_t peak_cap;
+    int32_t window;         // < 0: no pair counts
+    int32_t* paircnt;       // [peak_cap]
+    int64_t* extra_pairs;   // pairs of peaks beyond peak_cap (device scalar) or nullptr
+};
+
+struct AssocParams {
+    const float* x;
+    const float* y;
+    const int32_t* offs;
+    int64_t n_hits;
+    int32_t event0, n_events;
+    const uint32_t* mask;
+    const uint16_t* wpre;
+    const int32_t* npk;
+    const int64_t* colbase;
+    const int64_t* peak_offsets;
+    int64_t peak_cap;
+    int32_t* cursor;        // [peak_cap], zeroed
+    int32_t* hit_idx;
+    int64_t pair_cap;
+    int32_t window;
+    const float* cphi;
+    const float* sphi;
+    const float4* dtab;
+    KConsts K;
+    unsigned long long* stats;
+};
+
+// Exclusive scan of int32 counts over [lo, hi) (clamped to cap) into int64
+// outputs: out[i] = base + sum(in[lo..i)), out[hi] = total, *total = base + sum.
+// lo/hi/base come from device scalars when the pointers are non-null.
+struct ScanRange {
+    const int32_t* in;
+    int64_t* out;
+    const int64_t* lo_dev;
+    const int64_t* hi_dev;
+    const int64_t* base_dev;
+    int64_t lo, hi, base, cap;
+    int64_t* total;        // device scalar or nullptr
+    int32_t write_end;     // 1: also write out[hi] = total
+};
+
+constexpr int kScanBlocks = 304;
+constexpr int kScanThreads = 1024;
+
+int vote_smem_bytes(int tile_phi, int tile_d, int nk);
+cudaError_t vote_prepare(int tile_phi, int smem_bytes);
+cudaError_t vote_occupancy(int tile_phi, int threads, int smem, int* blocks);
+cudaError_t launch_finalize(int64_t* scal, cudaStream_t s);
+cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s);
+cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer, int64_t n_hits,
+                            const int32_t* offs, int32_t n_events, int32_t n_layers, int32_t* err,
+                            cudaStream_t s);
+cudaError_t launch_order(const int32_t* offs, int32_t event0, int32_t n_events, int64_t n_hits,
+                         int32_t* order, cudaStream_t s);
+cudaError_t launch_detect(const PeakParams& p, cudaStream_t s);
+cudaError_t launch_emit(const PeakParams& p, cudaStream_t s);
+cudaError_t launch_paircount(const PeakParams& p, const int64_t* lo_dev, const int64_t* hi_dev,
+                             cudaStream_t s);
+cudaError_t launch_scan(const ScanRange& r, int64_t* scratch /* 2 * kScanBlocks */, cudaStream_t s);
+cudaError_t launch_assoc(const AssocParams& p, cudaStream_t s);
+cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
+
+}  // namespace ht

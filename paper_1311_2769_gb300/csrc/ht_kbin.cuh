@@ -1,0 +1,226 @@
+// ht_kbin.cuh — the curvature bin of a (hit, phi0_i, d0_j) column on the GPU.
+//
+// Definition (Section 3 track model, curved and displaced): with
+//   q = y c - x s, a = q - d, den = (x^2 + y^2 + d^2) - 2 d q,
+//   kappa = 2 a / den, w = (kappa - kappa_min) * n_kappa / (kappa_max - kappa_min),
+// the hit votes into bin floor(w) when den > 0 and 0 <= w < n_kappa.  The bin
+// is *defined* by binary64 IEEE operations in exactly this order on the float32
+// hit (x, y) and float32 tables (c, s, d).  GB300 runs binary64 at a tiny
+// fraction of its float32 rate, so the bin is reached in three stages, each of
+// which either decides the binary64 bin with a proof or hands on:
+//
+//   1. float32 estimate with an a-priori error bound tau (fast path, every cell);
+//   2. double-float ("float-float") evaluation with a much smaller bound
+//      (cells whose stage-1 interval [w - tau, w + tau] straddles a bin edge,
+//      or whose denominator is too small for the stage-1 bound);
+//   3. the binary64 definition itself, op for op (cells stage 2 cannot decide:
+//      hits within a fraction of a millimetre of the perigee point, or w within
+//      ~1e-9 of a bin edge).
+//
+// Notation for the bounds: u = 2^-24 (float32 unit roundoff), e_r = 2^-22 (a
+// bound on the relative error of rcp.approx.ftz.f32, checked by a GPU test),
+// R1 = r + dabs with r = |h| and dabs = max_j |d0_j|, V = the largest |v| of a
+// cell that still matters (v = w - H, H = -kappa_min * scale).  Every bound
+// below carries a factor-2 safety margin over the first-order analysis.
+#pragma once
+#include <cstdint>
+
+namespace ht {
+
+// Grid constants shared by every kernel that bins a cell (filled on the host).
+struct KConsts {
+    int nphi, nd, nk;
+    // stage 1 (float32 estimate)
+    float S2;       // float(2 * scale), scale = n_kappa / (kappa_max - kappa_min)
+    float H;        // float(-kappa_min * scale)
+    float T0;       // constant part of tau
+    float cG1, cG2; // tau = T0 + (cG1 R1^2 + cG2 P1) * rcp(den), P1 = 3.02 r + 1.01 dabs
+    float cD1, cD2; // den_min = max(cD1 R1^2, cD2 P1): below it the bound is not used
+    float wlo, whi; // w outside (wlo, whi) = (-m, n_kappa + m) is out of range for sure
+    float dabs;
+    // stage 2 (double-float)
+    float S2hi, S2lo, Hhi, Hlo; // 2*scale and H as float pairs (hi + lo)
+    float T0b;                  // constant part of tau2
+    float cGb1, cGb2;           // tau2 = T0b + (cGb1 R1^2 + cGb2 R1) * rcp(den)
+    float cDb;                  // den_min2 = cDb * R1^2
+    // stage 3 (binary64 definition)
+    double kmin, scale;
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---- stage 1 -------------------------------------------------------------
+// Inputs hoisted out of the cell loop:
+//   per hit      r2 = fl(fma(x, x, fl(y*y))), G = cG1 R1^2 + cG2 P1, dmin
+//   per (hit,i)  q  = fl(fma(y, c, -fl(x*s)))            |q - q*|   <= 2.01 u r
+//   per (hit,j)  Rj = fl(r2 + fl(d*d))                    |Rj - R*|  <= 3.02 u r^2 + 2.01 u d^2
+// Per cell:
+//   a   = fl(q - d)                                       |a - a*|   <= u (3.02 r + 1.01 |d|)
+//   den = fl(fma(-2d, q, Rj))                             |den-den*| <= E = 4.03 u R1^2
+//   w   = fl(fma(fl(a * rcp(den)), S2, H))
+// With den > den_min >= 64 E the relative error of den is <= 1/64, and for a
+// cell whose w lies in (-m, n_kappa + m) (so |v| <= V):
+//   |w - w*| <= (e_r + 3u) V + u(|H| + 2 (n_kappa + m)) + u     (constant: T0)
+//             + (64/63) E V / den + 1.01 S2 u (3.02 r + 1.01 |d|) / den   (per-hit: G)
+// and w* (the exact real value) is within ~1e-11 bins of the binary64 w.
+// A cell whose w lies outside (-m, n_kappa + m) is out of range in binary64
+// too: m is chosen on the host so that m (1 - e_v) exceeds e_v V0 + 0.26, where
+// e_v <= e_r + 4u + 1/63 bounds the relative error of v and 0.26 bounds the
+// absolute part (den >= den_min also caps the a-error term at 0.25 bins).
+// Returns k >= 0 (vote), -1 (no vote) or -2 (undecided: use cell_slow).
+__device__ __forceinline__ int cell_fast(float q, float dj, float d2j, float Rj, float G, float dmin,
+                                         const KConsts& K) {
+    const float a = q - dj;
+    const float den = fmaf(-d2j, q, Rj);
+    const float rc = rcp_approx(den);
+    const float t = a * rc;
+    const float w = fmaf(t, K.S2, K.H);
+    const float tau = fmaf(G, rc, K.T0);
+    // floor(w -+ tau) by round-down addition of 1.5 * 2^23 (exact for |.| < 2^22)
+    const float flo = __fadd_rd(w - tau, 12582912.0f);
+    const float fhi = __fadd_rd(w + tau, 12582912.0f);
+    const int k = __float_as_int(flo) - 0x4B400000;
+    const bool denok = den > dmin;
+    if (denok && flo == fhi) return ((unsigned)k < (unsigned)K.nk) ? k : -1;
+    if (denok && !(w > K.wlo && w < K.whi)) return -1;
+    return -2;
+}
+
+// ---- stage 2: double-float ---------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
+// Exact products and error-free sums give q, a and den with absolute errors
+// <= 8 u^2 r, 8 u^2 (r + |d|) and 24 u^2 R1^2; the quotient a/den is formed
+// as q1 + q2 (q1 = a_hi rcp(den_hi), q2 = remainder * rcp) with relative
+// error <= 2^-40; v = (q1 + q2) * (S2hi + S2lo) and w = v + (Hhi + Hlo) add
+// ~2^-44 V.  With den >= den_min2 = cDb R1^2 (relative den error <= 2^-20):
+//   |w_dd - w64| <= T0b + (cGb1 R1^2 + cGb2 R1) / den = tau2,
+// and w outside (-2, n_kappa + 2) is out of range for sure.
+// Returns k >= 0, -1, or -2 (undecided: use binary64).
+__device__ __forceinline__ int cell_dd(float x, float y, float c, float s, float d, float R1,
+                                       const KConsts& K) {
+    float p1, e1, p2, e2;
+    two_prod(y, c, p1, e1);
+    two_prod(x, s, p2, e2);
+    float s1, t1;
+    two_sum(p1, -p2, s1, t1);
+    float qh, ql;
+    two_sum(s1, __fadd_rn(t1, __fsub_rn(e1, e2)), qh, ql);
+    float s2, t2;
+    two_sum(qh, -d, s2, t2);
+    float ah, al;
+    two_sum(s2, __fadd_rn(t2, ql), ah, al);
+    float xx, exx, yy, eyy, dd, edd;
+    two_prod(x, x, xx, exx);
+    two_prod(y, y, yy, eyy);
+    two_prod(d, d, dd, edd);
+    const float d2 = __fadd_rn(d, d);
+    float mh, me;
+    two_prod(d2, qh, mh, me);
+    me = fmaf(d2, ql, me);
+    float s3, t3, s4, t4, s5, t5;
+    two_sum(xx, yy, s3, t3);
+    two_sum(s3, dd, s4, t4);
+    two_sum(s4, -mh, s5, t5);
+    const float low = __fadd_rn(__fadd_rn(__fadd_rn(exx, eyy), __fsub_rn(edd, me)),
+                                __fadd_rn(__fadd_rn(t3, t4), t5));
+    float denh, denl;
+    two_sum(s5, low, denh, denl);
+    if (!(denh > K.cDb * R1 * R1)) return -2;
+    const float rc = rcp_approx(denh);
+    const float q1 = __fmul_rn(ah, rc);
+    float pp, pe;
+    two_prod(q1, denh, pp, pe);
+    const float rem = fmaf(-q1, denl, __fadd_rn(__fsub_rn(__fsub_rn(ah, pp), pe), al));
+    const float q2 = __fmul_rn(rem, rc);
+    float vh, ve;
+    two_prod(q1, K.S2hi, vh, ve);
+    ve = fmaf(q1, K.S2lo, ve);
+    ve = fmaf(q2, K.S2hi, ve);
+    float s6, t6;
+    two_sum(vh, K.Hhi, s6, t6);
+    float wh, wl;
+    two_sum(s6, __fadd_rn(__fadd_rn(t6, ve), K.Hlo), wh, wl);
+    if (!(wh > -2.0f && wh < (float)K.nk + 2.0f)) return -1;
+    const float tau2 = fmaf(fmaf(K.cGb1 * R1, R1, K.cGb2 * R1), rc, K.T0b);
+    // floor of wh + wl: wh may round up onto an integer while wl < 0
+    float kf = floorf(wh);
+    float a0, b0, a1, b1;
+    two_sum(wh, -kf, a0, b0);
+    float dist_lo = __fadd_rn(a0, __fadd_rn(b0, wl));
+    two_sum(__fadd_rn(kf, 1.0f), -wh, a1, b1);
+    float dist_hi = __fadd_rn(a1, __fsub_rn(b1, wl));
+    if (dist_lo < 0.0f) {
+        kf = __fsub_rn(kf, 1.0f);
+        dist_hi = -dist_lo;
+        dist_lo = __fadd_rn(dist_lo, 1.0f);
+    }
+    if (dist_lo > tau2 && dist_hi > tau2) {
+        const int k = (int)kf;
+        return (k >= 0 && k < K.nk) ? k : -1;
+    }
+    return -2;
+}
+
+// ---- stage 3: the binary64 definition, op for op ------------------------
+__device__ __forceinline__ int cell_f64(float xf, float yf, float cf, float sf, float df,
+                                        const KConsts& K) {
+    const double x = xf, y = yf, c = cf, s = sf, d = df;
+    const double q = __dsub_rn(__dmul_rn(y, c), __dmul_rn(x, s));
+    const double a = __dsub_rn(q, d);
+    const double den = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(d, d)),
+                                 __dmul_rn(__dmul_rn(2.0, d), q));
+    if (!(den > 0.0)) return -1;
+    const double kappa = __ddiv_rn(__dmul_rn(2.0, a), den);
+    const double w = __dmul_rn(__dsub_rn(kappa, K.kmin), K.scale);
+    if (!(w >= 0.0 && w < (double)K.nk)) return -1;
+    return (int)w;
+}
+
+// Stages 2 and 3, kept out of line so the hot loop stays small.
+// stats (optional): [0] cells (counted by callers), [1] stage-2 decisions, [2] stage-3 decisions.
+static __device__ __noinline__ int cell_slow(float x, float y, float c, float s, float d, float R1,
+                                      const KConsts& K, unsigned long long* stats) {
+    int k = cell_dd(x, y, c, s, d, R1, K);
+    if (k != -2) {
+        if (stats) atomicAdd(&stats[1], 1ull);
+        return k;
+    }
+    if (stats) atomicAdd(&stats[2], 1ull);
+    return cell_f64(x, y, c, s, d, K);
+}
+
+// Per-hit quantities of stage 1.
+struct HitFast {
+    float r2, R1, G, dmin;
+};
+
+__device__ __forceinline__ HitFast hit_fast(float x, float y, const KConsts& K) {
+    HitFast h;
+    h.r2 = fmaf(x, x, __fmul_rn(y, y));
+    const float r = sqrtf(h.r2);
+    h.R1 = r + K.dabs;
+    const float P1 = fmaf(3.02f, r, 1.01f * K.dabs);
+    const float R1s = h.R1 * h.R1;
+    h.G = fmaf(K.cG1, R1s, K.cG2 * P1);
+    h.dmin = fmaxf(K.cD1 * R1s, K.cD2 * P1);
+    return h;
+}
+
+__device__ __forceinline__ float q_of(float x, float y, float c, float s) {
+    return fmaf(y, c, -__fmul_rn(x, s));
+}
+
+}  // namespace ht

@@ -1,0 +1,52 @@
+"""The C ABI library builds, loads without a GPU and exports every entry
+point include/ht.h declares (no compute call is made here)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ht.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ht_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1311_2769_gb300 import build, ht
+    build.build()
+    return ht.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("ht_create", "ht_destroy", "ht_vote", "ht_peaks", "ht_associate", "ht_process",
+                     "ht_get_accumulator", "ht_get_tables", "ht_sync", "ht_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1311_2769_gb300 import ht
+    assert sorted(set(ht.EXPORTS)) == _declared()
+
+
+def test_strerror_needs_no_gpu(lib):
+    assert lib.ht_strerror(0) == b"ok"
+    assert lib.ht_strerror(-3) == b"output capacity exceeded"
+    assert lib.ht_strerror(12345) == b"unknown status"
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    assert lib.ht_destroy(None) == -1
+    assert lib.ht_sync(None) == -1
+    assert lib.ht_create(None, None, None) == -1
