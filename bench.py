@@ -183,7 +183,7 @@ def run_gpu(args):
     build.build()
     w = synth.WORKLOADS[WORKLOAD]
     g = w.grid
-    batch = synth.generate(w, seed=w.seed + 1000 * rank if rank else None)
+    batch = synth.generate(w, n_events=args.events, seed=w.seed + 1000 * rank if rank else None)
     n_events, n_hits = batch.n_events, batch.n_hits
     cols = g.n_phi * g.n_d0
     hit_votes = float(n_hits) * cols
@@ -191,9 +191,13 @@ def run_gpu(args):
     ctx = ht.Context(g, w.spec.layers)
     ctx.set_option(ht.HT_OPT_PHASE_TIMING, 1)
     hits_d = ht.Hits.from_batch(batch, device=dev)
-    # autotune the vote tile on a 256-event sample (outside the timed region)
-    sample = batch.select(range(0, n_events, max(1, n_events // 256)))
-    ctx.autotune(ht.Hits.from_batch(sample, device=dev))
+    if args.tile:
+        for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
+            ctx.set_option(k, int(v))
+    else:
+        # autotune the vote tile on a 256-event sample (outside the timed region)
+        sample = batch.select(range(0, n_events, max(1, n_events // 256)))
+        ctx.autotune(ht.Hits.from_batch(sample, device=dev))
     tile = {"tile_phi": ctx.get_option(ht.HT_OPT_TILE_PHI), "tile_d0": ctx.get_option(ht.HT_OPT_TILE_D0),
             "threads": ctx.get_option(ht.HT_OPT_THREADS)}
 
@@ -245,6 +249,14 @@ def run_gpu(args):
         ms = float(t.item())
     launches = ctx.get_option(ht.HT_OPT_LAUNCHES)
     counts = res.counts.cpu().numpy()
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * n_events / (ms / 1e3), "ms_per_step": ms,
+                              "events": n_events, "phase_ms": {"vote": float(np.mean(vote_ms)),
+                                                               "peaks_assoc": float(np.mean(rest_ms))},
+                              "peaks": int(counts[0]), "pairs": int(counts[1]), "tile": tile}), flush=True)
+        ctx.close()
+        return 0
 
     # ---- plain form (one launch sequence per event) on a 512-event sample
     plain_ctx = ht.Context(g, w.spec.layers)
@@ -353,6 +365,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events", type=int, default=None, help="events per batch (default: the full 4096)")
+    ap.add_argument("--tile", default="", help="vote tile 'phi,d0,threads' instead of autotuning")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed batched steps (no plain form, e2e or CPU baseline); for profiling")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

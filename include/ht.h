@@ -101,7 +101,10 @@ typedef struct {
  * hit_idx[pair_cap] (global hit indices of the batch, ascending within each
  * peak); counts[2] = {n_peaks, n_pairs}, the true totals even on overflow.
  * Peaks beyond peak_cap and pairs beyond pair_cap are dropped and the call
- * reports HT_ERR_OVERFLOW (at ht_sync for device outputs). */
+ * reports HT_ERR_OVERFLOW (at ht_sync for device outputs): the first
+ * peak_cap peaks and every CSR row that ends at or below pair_cap are still
+ * exact; the one row that crosses pair_cap holds an unspecified subset of its
+ * hits in its slots below the cap.  Re-run with larger caps for the rest. */
 typedef struct {
     ht_peak *peaks;
     int64_t peak_cap;
@@ -116,7 +119,7 @@ typedef struct {
 #define HT_OPT_MODE 1              /* HT_MODE_BATCHED (default) or HT_MODE_PLAIN */
 #define HT_OPT_TILE_PHI 2          /* phi0 rows per vote tile: 1, 2, 4 or 8 (0 = auto) */
 #define HT_OPT_TILE_D0 3           /* d0 columns per vote tile, 1..n_d0 (0 = auto) */
-#define HT_OPT_THREADS 4           /* threads per vote CTA: 128, 256, 512 (0 = auto) */
+#define HT_OPT_THREADS 4           /* threads per vote CTA: 128 or 256 (0 = auto) */
 #define HT_OPT_ACC_BUDGET 5        /* accumulator memory budget in bytes (0 = 40 GB) */
 #define HT_OPT_COUNT_STAGES 6      /* 1 = count precision-stage usage (ht_filter_stats) */
 #define HT_OPT_USE_GRAPH 7         /* 1 = replay the batched step as a CUDA graph (default 1) */

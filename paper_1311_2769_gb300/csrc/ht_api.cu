@@ -80,6 +80,7 @@ struct ht_ctx {
 
     // resolved tile configuration
     int r_tile_phi = 1, r_tile_d = 1, r_threads = 256, r_smem = 0, r_blocks_per_sm = 1;
+    int a_tile_d = 1, a_threads = 256, a_smem = 0;  // association tile (same phi rows)
 
     int gen = 0;  // buffer generation (graph invalidation)
     DBuf<float> sx, sy;
@@ -193,7 +194,7 @@ KConsts make_consts(const ht_grid& g, const std::vector<float>& d0) {
     K.dabs = (float)dabs;
     const double V0 = std::max(std::fabs(Hd), std::fabs((double)nk - Hd));
     const double ev = er + 4.0 * u + 1.0 / 63.0;
-    const double m = std::ceil(2.0 * (ev * ((double)nk + std::fabs(Hd)) + 0.26) / (1.0 - ev)) + 1.0;
+    const double m = std::ceil(2.0 * (ev * ((double)nk + std::fabs(Hd)) + 0.3) / (1.0 - ev)) + 1.0;
     const double Vmax = V0 + m;
     K.wlo = (float)(-m);
     K.whi = (float)((double)nk + m);
@@ -202,7 +203,7 @@ KConsts make_consts(const ht_grid& g, const std::vector<float>& d0) {
     K.cG1 = (float)(2.0 * (64.0 / 63.0) * 4.03 * u * Vmax * (1.0 + er) * (1.0 + er + 4.0 * u));
     K.cG2 = (float)(2.0 * 1.01 * S2 * u * (1.0 + er));
     K.cD1 = (float)(64.0 * 4.03 * u);
-    K.cD2 = (float)(4.1 * 1.01 * S2 * u * (1.0 + er));
+    K.cD2 = (float)(3.6 * 1.01 * S2 * u * (1.0 + er));
     // stage 2
     const double two_scale = 2.0 * scale;
     K.S2hi = (float)two_scale;
@@ -247,15 +248,26 @@ int resolve_tiles(ht_ctx* ctx) {
     const int smem = vote_smem_bytes(tp, td, nk);
     if (smem > 227 * 1024)
         return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d needs %d B of shared memory", tp, td, nk, smem);
-    CU(vote_prepare(tp, smem));
+    CU(vote_prepare(tp, nk, smem));
     int per_sm = 0;
-    CU(vote_occupancy(tp, thr, smem, &per_sm));
+    CU(vote_occupancy(tp, nk, thr, smem, &per_sm));
     if (per_sm < 1) return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d with %d threads cannot launch", tp, td, nk, thr);
     ctx->r_tile_phi = tp;
     ctx->r_tile_d = td;
     ctx->r_threads = thr;
     ctx->r_smem = smem;
     ctx->r_blocks_per_sm = per_sm;
+    // association tile: same phi rows, d0 width halved until its metadata,
+    // cursors and sort buffers fit in 200 KB of shared memory
+    int atd = td;
+    const int athr = std::min(thr, 256);
+    while (atd > 1 && assoc_smem(tp, atd, nk, athr) > 200 * 1024) atd = (atd + 1) / 2;
+    const int asmem = (int)assoc_smem(tp, atd, nk, athr);
+    if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association tile does not fit shared memory");
+    CU(assoc_prepare(tp, nk, asmem));
+    ctx->a_tile_d = atd;
+    ctx->a_threads = athr;
+    ctx->a_smem = asmem;
     return HT_OK;
 }
 
@@ -422,8 +434,6 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, i
     r.total = ctx->d_scal + 1;
     r.write_end = 1;
     CU(launch_scan(r, ctx->scratch.p, s));
-    // the pair counts are consumed: reuse the buffer as per-peak cursors
-    if (peak_cap > 0) CU(cudaMemsetAsync(ctx->paircnt.p, 0, peak_cap * sizeof(int32_t), s));
     AssocParams a{};
     a.x = ctx->cx;
     a.y = ctx->cy;
@@ -437,7 +447,6 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, i
     a.colbase = ctx->colbase.p;
     a.peak_offsets = peak_offsets;
     a.peak_cap = peak_cap;
-    a.cursor = ctx->paircnt.p;
     a.hit_idx = hit_idx;
     a.pair_cap = pair_cap;
     a.window = window;
@@ -446,7 +455,7 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, i
     a.dtab = ctx->d_dtab;
     a.K = ctx->K;
     a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
-    CU(launch_assoc(a, s));
+    CU(launch_assoc(a, ctx->r_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
     return HT_OK;
 }
 
@@ -594,6 +603,12 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
         ht_destroy(ctx);
         return st;
     }
+    if (detect_smem(grid->n_phi, grid->n_d0, grid->n_kappa) > 227 * 1024 ||
+        detect_prepare(grid->n_phi, grid->n_d0, grid->n_kappa) != cudaSuccess) {
+        cudaGetLastError();
+        ht_destroy(ctx);
+        return HT_ERR_INVALID_ARG;
+    }
     *out = ctx;
     return HT_OK;
 }
@@ -645,8 +660,8 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             ctx->tile_d = (int)value;
             break;
         case HT_OPT_THREADS:
-            if (value != 0 && value != 128 && value != 256 && value != 512)
-                return fail(ctx, HT_ERR_INVALID_ARG, "threads must be 0, 128, 256 or 512");
+            if (value != 0 && value != 128 && value != 256)
+                return fail(ctx, HT_ERR_INVALID_ARG, "threads must be 0, 128 or 256");
             ctx->threads = (int)value;
             break;
         case HT_OPT_ACC_BUDGET:
@@ -774,7 +789,6 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     CU(cudaStreamSynchronize(s));
     const int64_t total = ctx->h_pinned[1];
     CU(ctx->hitidx.ensure(std::max<int64_t>(total, 1), &ctx->gen));
-    if (np > 0) CU(cudaMemsetAsync(ctx->paircnt.p, 0, np * sizeof(int32_t), s));
     AssocParams a{};
     a.x = ctx->cx;
     a.y = ctx->cy;
@@ -788,7 +802,6 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     a.colbase = ctx->colbase.p;
     a.peak_offsets = ctx->peakoff.p;
     a.peak_cap = np;
-    a.cursor = ctx->paircnt.p;
     a.hit_idx = ctx->hitidx.p;
     a.pair_cap = total;
     a.window = window;
@@ -797,7 +810,7 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     a.dtab = ctx->d_dtab;
     a.K = ctx->K;
     a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
-    CU(launch_assoc(a, s));
+    CU(launch_assoc(a, ctx->r_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
     CU(cudaMemcpyAsync(peak_offsets, ctx->peakoff.p, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     const int64_t ncopy = std::min(total, cap);
     if (ncopy > 0) CU(cudaMemcpyAsync(hit_idx, ctx->hitidx.p, ncopy * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -996,7 +1009,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
         for (int td : tds) {
             const int smem = vote_smem_bytes(tp, td, nk);
             if (smem > 200 * 1024 || smem < 8 * 1024) continue;
-            for (int thr : {256, 512}) {
+            for (int thr : {128, 256}) {
                 ctx->tile_phi = tp;
                 ctx->tile_d = td;
                 ctx->threads = thr;

@@ -59,7 +59,6 @@ struct AssocParams {
     const int64_t* colbase;
     const int64_t* peak_offsets;
     int64_t peak_cap;
-    int32_t* cursor;        // [peak_cap], zeroed
     int32_t* hit_idx;
     int64_t pair_cap;
     int32_t window;
@@ -88,8 +87,8 @@ constexpr int kScanBlocks = 304;
 constexpr int kScanThreads = 1024;
 
 int vote_smem_bytes(int tile_phi, int tile_d, int nk);
-cudaError_t vote_prepare(int tile_phi, int smem_bytes);
-cudaError_t vote_occupancy(int tile_phi, int threads, int smem, int* blocks);
+cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes);
+cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks);
 cudaError_t launch_finalize(int64_t* scal, cudaStream_t s);
 cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s);
 cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer, int64_t n_hits,
@@ -97,12 +96,16 @@ cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer,
                             cudaStream_t s);
 cudaError_t launch_order(const int32_t* offs, int32_t event0, int32_t n_events, int64_t n_hits,
                          int32_t* order, cudaStream_t s);
+size_t detect_smem(int nphi, int nd, int nk);
+cudaError_t detect_prepare(int nphi, int nd, int nk);
 cudaError_t launch_detect(const PeakParams& p, cudaStream_t s);
 cudaError_t launch_emit(const PeakParams& p, cudaStream_t s);
 cudaError_t launch_paircount(const PeakParams& p, const int64_t* lo_dev, const int64_t* hi_dev,
                              cudaStream_t s);
 cudaError_t launch_scan(const ScanRange& r, int64_t* scratch /* 2 * kScanBlocks */, cudaStream_t s);
-cudaError_t launch_assoc(const AssocParams& p, cudaStream_t s);
+size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads);
+cudaError_t assoc_prepare(int tile_phi, int nk, int smem);
+cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int tile_d, int threads, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
 
 }  // namespace ht

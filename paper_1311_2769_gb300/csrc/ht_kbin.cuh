@@ -68,9 +68,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //             + (64/63) E V / den + 1.01 S2 u (3.02 r + 1.01 |d|) / den   (per-hit: G)
 // and w* (the exact real value) is within ~1e-11 bins of the binary64 w.
 // A cell whose w lies outside (-m, n_kappa + m) is out of range in binary64
-// too: m is chosen on the host so that m (1 - e_v) exceeds e_v V0 + 0.26, where
-// e_v <= e_r + 4u + 1/63 bounds the relative error of v and 0.26 bounds the
-// absolute part (den >= den_min also caps the a-error term at 0.25 bins).
+// too: m is chosen on the host so that m (1 - e_v) exceeds e_v (n_kappa + |H|) + 0.3, where
+// e_v <= e_r + 4u + 1/63 bounds the relative error of v and 0.3 bounds the
+// absolute part (den >= den_min also caps the a-error term at 0.28 bins).
 // Returns k >= 0 (vote), -1 (no vote) or -2 (undecided: use cell_slow).
 __device__ __forceinline__ int cell_fast(float q, float dj, float d2j, float Rj, float G, float dmin,
                                          const KConsts& K) {
@@ -79,7 +79,7 @@ __device__ __forceinline__ int cell_fast(float q, float dj, float d2j, float Rj,
     const float rc = rcp_approx(den);
     const float t = a * rc;
     const float w = fmaf(t, K.S2, K.H);
-    const float tau = fmaf(G, rc, K.T0);
+    const float tau = fmaf(G, fabsf(rc), K.T0);
     // floor(w -+ tau) by round-down addition of 1.5 * 2^23 (exact for |.| < 2^22)
     const float flo = __fadd_rd(w - tau, 12582912.0f);
     const float fhi = __fadd_rd(w + tau, 12582912.0f);
@@ -88,6 +88,26 @@ __device__ __forceinline__ int cell_fast(float q, float dj, float d2j, float Rj,
     if (denok && flo == fhi) return ((unsigned)k < (unsigned)K.nk) ? k : -1;
     if (denok && !(w > K.wlo && w < K.whi)) return -1;
     return -2;
+}
+
+// Stage 1 in the form the tile kernels use: `vote` when the certified bin
+// kb lies in [0, n_kappa), `pend` when stage 2 must decide.  The den > den_min
+// test is implicit for certification (G >= 0.55 den_min makes tau > 1/2
+// below it) and explicit only for the window shortcut, which needs it.
+__device__ __forceinline__ void stage1(float q, float4 dt, float Rj, float G, float dmin, float S2, float H,
+                                       float T0, float wlo, float whi, unsigned nk, unsigned& kb, bool& vote,
+                                       bool& pend) {
+    const float a = q - dt.x;
+    const float den = fmaf(-dt.y, q, Rj);
+    const float rc = rcp_approx(den);
+    const float w = fmaf(a * rc, S2, H);
+    const float tau = fmaf(G, fabsf(rc), T0);
+    const float flo = __fadd_rd(w - tau, 12582912.0f);
+    const float fhi = __fadd_rd(w + tau, 12582912.0f);
+    kb = __float_as_uint(flo) - 0x4B400000u;
+    const bool decided = flo == fhi;
+    vote = decided & (kb < nk);
+    pend = !decided & (!(den > dmin) | ((w > wlo) & (w < whi)));
 }
 
 // ---- stage 2: double-float ---------------------------------------------
@@ -214,8 +234,10 @@ __device__ __forceinline__ HitFast hit_fast(float x, float y, const KConsts& K) 
     h.R1 = r + K.dabs;
     const float P1 = fmaf(3.02f, r, 1.01f * K.dabs);
     const float R1s = h.R1 * h.R1;
-    h.G = fmaf(K.cG1, R1s, K.cG2 * P1);
     h.dmin = fmaxf(K.cD1 * R1s, K.cD2 * P1);
+    // G >= 0.55 dmin: a cell with den <= dmin (or den <= 0, via |rcp|) gets
+    // tau > 1/2, so stage 1 can never certify it
+    h.G = fmaxf(fmaf(K.cG1, R1s, K.cG2 * P1), 0.55f * h.dmin);
     return h;
 }
 

@@ -11,6 +11,7 @@
 // atomic queue whose events are ordered largest first.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -33,18 +34,86 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // ---------------------------------------------------------------------------
 // vote
 // ---------------------------------------------------------------------------
-template <int SPHI>
-__global__ void __launch_bounds__(512) vote_kernel(const VoteParams p) {
+// Shared tile layout: [d0 column j][phi row r][kappa k], kappa contiguous, so
+// a row's offset r * NK is a compile-time immediate of the atomic.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Predicated shared reduction: no branch around the atomic in the hot loop.
+__device__ __forceinline__ void red_shared_if(uint32_t addr, bool pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(addr),
+        "r"((unsigned)pred));
+}
+
+struct TileHit {
+    float x, y;
+    HitFast hf;
+};
+
+// One hit against every column of the tile.  TAIL: lanes past the event's
+// last hit stay in the loop (the full-mask vote needs all 32) but are masked.
+template <int SPHI, int NK, bool TAIL>
+__device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* cp, const float* sp,
+                                             const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int nj, int nk,
+                                             int64_t h, bool valid) {
+    const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
+    const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
+    const HitFast hf = hit_fast(x, y, p.K);
+    float q[SPHI];
+#pragma unroll
+    for (int r = 0; r < SPHI; ++r) q[r] = q_of(x, y, cp[r], sp[r]);
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0, wlo = p.K.wlo, whi = p.K.whi;
+    const unsigned nku = (unsigned)nk;
+    const int col_words = SPHI * nk;
+    uint32_t col_sh = acc_sh;
+    for (int j = 0; j < nj; ++j, col_sh += 4u * col_words) {
+        const float4 dt = dt_s[j];
+        const float Rj = hf.r2 + dt.z;
+        bool anyp = false;
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            unsigned kb;
+            bool vote, pend;
+            stage1(q[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
+            if (TAIL) {
+                vote &= valid;
+                pend &= valid;
+            }
+            red_shared_if(col_sh + 4u * ((unsigned)(r * nk) + kb), vote);
+            anyp |= pend;
+        }
+        if (__any_sync(0xffffffffu, anyp)) {
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                unsigned kb;
+                bool vote, pend;
+                stage1(q[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
+                if (pend && (!TAIL || valid)) {
+                    const int kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                    if (kk >= 0) atomicAdd(acc_s + j * col_words + r * nk + kk, 1u);
+                }
+            }
+        }
+    }
+}
+
+template <int SPHI, int NK>
+__global__ void __launch_bounds__(256, 3) vote_kernel(const VoteParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* dt_s = reinterpret_cast<float4*>(smem_raw);
     uint32_t* acc_s = reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d);
     __shared__ int s_item;
 
-    const int nk = p.K.nk;
+    const int nk = NK ? NK : p.K.nk;
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int tiles = p.tiles_phi * p.tiles_d;
-    const int row_words = p.tile_d * nk;
+    const int col_words = SPHI * nk;
+    const uint32_t acc_sh = smem_addr(acc_s);
 
     for (int it = 0;; ++it) {
         int item;
@@ -69,54 +138,43 @@ __global__ void __launch_bounds__(512) vote_kernel(const VoteParams p) {
         const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
         const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
 
-        for (int w = tid; w < SPHI * row_words; w += nthr) acc_s[w] = 0u;
+        for (int w = tid; w < nj * col_words; w += nthr) acc_s[w] = 0u;
         for (int j = tid; j < nj; j += nthr) dt_s[j] = p.dtab[j0 + j];
+        // rows past a ragged phi edge vote into tile slots that are never flushed
         float cp[SPHI], sp[SPHI];
 #pragma unroll
         for (int r = 0; r < SPHI; ++r) {
-            cp[r] = r < nrows ? p.cphi[i0 + r] : 0.0f;
-            sp[r] = r < nrows ? p.sphi[i0 + r] : 0.0f;
+            const int i = r < nrows ? i0 + r : i0;
+            cp[r] = p.cphi[i];
+            sp[r] = p.sphi[i];
         }
         if (p.stats && tid == 0) atomicAdd(&p.stats[0], (unsigned long long)((he - hb) * nrows * nj));
         __syncthreads();
 
-        for (int64_t h = hb + tid; h < he; h += nthr) {
-            const float x = p.x[h];
-            const float y = p.y[h];
-            const HitFast hf = hit_fast(x, y, p.K);
-            float q[SPHI];
-#pragma unroll
-            for (int r = 0; r < SPHI; ++r) q[r] = q_of(x, y, cp[r], sp[r]);
-            for (int j = 0; j < nj; ++j) {
-                const float4 dt = dt_s[j];
-                const float Rj = hf.r2 + dt.z;
-                uint32_t* col = acc_s + j * nk;
-#pragma unroll
-                for (int r = 0; r < SPHI; ++r) {
-                    if (r < nrows) {
-                        int k = cell_fast(q[r], dt.x, dt.y, Rj, hf.G, hf.dmin, p.K);
-                        if (k == -2) k = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
-                        if (k >= 0) atomicAdd(col + r * row_words + k, 1u);
-                    }
-                }
-            }
+        const int64_t nfull = ((he - hb) / nthr) * nthr;
+        for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
+            vote_one_hit<SPHI, NK, false>(p, cp, sp, dt_s, acc_s, acc_sh, nj, nk, h, true);
+        {
+            const int64_t h = hb + nfull + tid;
+            if (hb + nfull + (tid - lane) < he)  // warps with at least one hit left
+                vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, nj, nk, h, h < he);
         }
         __syncthreads();
 
         uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
-        const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+        const int warp = tid >> 5, nw = nthr >> 5;
         const int nrj = nrows * nj;
         for (int row = warp; row < nrj; row += nw) {
             const int r = row / nj;
             const int j = row - r * nj;
-            const uint32_t* src = acc_s + r * row_words + j * nk;
+            const uint32_t* src = acc_s + j * col_words + r * nk;
             uint32_t* dst = dst_e + ((int64_t)(i0 + r) * p.K.nd + (j0 + j)) * nk;
             if ((nk & 3) == 0) {
                 const uint4* s4 = reinterpret_cast<const uint4*>(src);
                 uint4* d4 = reinterpret_cast<uint4*>(dst);
-                for (int k = lane; k < (nk >> 2); k += 32) d4[k] = s4[k];
+                for (int kk = lane; kk < (nk >> 2); kk += 32) d4[kk] = s4[kk];
             } else {
-                for (int k = lane; k < nk; k += 32) dst[k] = src[k];
+                for (int kk = lane; kk < nk; kk += 32) dst[kk] = src[kk];
             }
         }
         __syncthreads();
@@ -183,57 +241,95 @@ __global__ void order_kernel(const int32_t* offs, int32_t event0, int32_t n_even
 // ---------------------------------------------------------------------------
 // peaks: detection (warp per (event, phi0, d0) column, lanes over kappa)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool is_peak_cell(const uint32_t* A, const PeakParams& p, int i, int j, int k,
-                                             uint32_t v) {
-    const int64_t self = ((int64_t)i * p.nd + j) * p.nk + k;
-    for (int di = -1; di <= 1; ++di) {
-        int ii = i + di;
-        ii = ii < 0 ? ii + p.nphi : (ii >= p.nphi ? ii - p.nphi : ii);
-        for (int dj = -1; dj <= 1; ++dj) {
-            const int jj = j + dj;
-            if (jj < 0 || jj >= p.nd) continue;
-            for (int dk = -1; dk <= 1; ++dk) {
-                const int kk = k + dk;
-                if (kk < 0 || kk >= p.nk) continue;
-                const int64_t other = ((int64_t)ii * p.nd + jj) * p.nk + kk;
-                if (other == self) continue;
-                const uint32_t u = A[other];
-                if (other < self ? !(v > u) : !(v >= u)) return false;
-            }
-        }
-    }
-    return true;
-}
+// A CTA stages rows i0-1 .. i0+R (phi wraps) x columns j0-1 .. j0+TD of one
+// event in shared memory, cells outside the d0 range marked absent, and tests
+// every interior cell at or above the threshold against its 26 neighbours
+// with the linear-order tie rule, leaving at the first failure.
+constexpr uint32_t kAbsent = 0xFFFFFFFFu;
 
-__global__ void detect_kernel(const PeakParams p) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t per_ev = (int64_t)p.nphi * p.nd;
-    const int64_t ncols = per_ev * p.n_events;
-    for (int64_t col = gw; col < ncols; col += nwt) {
-        const int e = (int)(col / per_ev);
-        const int ij = (int)(col - e * per_ev);
-        const int i = ij / p.nd;
-        const int j = ij - i * p.nd;
+__global__ void __launch_bounds__(256) detect_kernel(const PeakParams p, const int R, const int TD) {
+    extern __shared__ __align__(16) uint32_t tile[];
+    const int nk = p.nk, nkw = p.nkw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tcols = TD + 2;
+    const int tiles_i = (p.nphi + R - 1) / R, tiles_j = (p.nd + TD - 1) / TD;
+    const int64_t items = (int64_t)p.n_events * tiles_i * tiles_j;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int e = (int)(item / ((int64_t)tiles_i * tiles_j));
+        const int t = (int)(item - (int64_t)e * tiles_i * tiles_j);
+        const int ti = t / tiles_j, tj = t - (t / tiles_j) * tiles_j;
+        const int i0 = ti * R, j0 = tj * TD;
+        const int nr = min(R, p.nphi - i0), nj = min(TD, p.nd - j0);
         const uint32_t* A = p.acc + (int64_t)e * p.cells;
-        const uint32_t* colp = A + ((int64_t)i * p.nd + j) * p.nk;
-        int count = 0;
-        for (int k0 = 0, w = 0; k0 < p.nk; k0 += 32, ++w) {
-            const int k = k0 + lane;
-            bool pk = false;
-            if (k < p.nk) {
-                const uint32_t v = colp[k];
-                if (v >= p.thr) pk = is_peak_cell(A, p, i, j, k, v);
+        __syncthreads();
+        // stage (nr + 2) x (nj + 2) columns
+        const int ncolumns = (nr + 2) * (nj + 2);
+        for (int cc = warp; cc < ncolumns; cc += nw) {
+            const int ri = cc / (nj + 2), cj = cc - (cc / (nj + 2)) * (nj + 2);
+            int ii = i0 - 1 + ri;
+            ii = ((ii % p.nphi) + p.nphi) % p.nphi;
+            const int jj = j0 - 1 + cj;
+            uint32_t* dst = tile + ((int64_t)ri * tcols + cj) * nk;
+            if (jj < 0 || jj >= p.nd) {
+                for (int kk = lane; kk < nk; kk += 32) dst[kk] = kAbsent;
+            } else {
+                const uint32_t* src = A + ((int64_t)ii * p.nd + jj) * nk;
+                if ((nk & 3) == 0) {
+                    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+                    uint4* d4 = reinterpret_cast<uint4*>(dst);
+                    for (int kk = lane; kk < (nk >> 2); kk += 32) d4[kk] = s4[kk];
+                } else {
+                    for (int kk = lane; kk < nk; kk += 32) dst[kk] = src[kk];
+                }
             }
-            const unsigned b = __ballot_sync(0xffffffffu, pk);
-            if (lane == 0) {
-                p.mask[col * p.nkw + w] = b;
-                p.wpre[col * p.nkw + w] = (uint16_t)count;
-            }
-            count += __popc(b);
         }
-        if (lane == 0) p.npk[col] = count;
+        __syncthreads();
+        // interior columns: warp per (row, column), lanes over kappa
+        for (int cc = warp; cc < nr * nj; cc += nw) {
+            const int r = cc / nj, j = cc - (cc / nj) * nj;
+            const int i = i0 + r;
+            // actual neighbour rows and whether they precede row i in linear order
+            const int im = i == 0 ? p.nphi - 1 : i - 1, ip = i == p.nphi - 1 ? 0 : i + 1;
+            const int64_t col = ((int64_t)e * p.nphi + i) * p.nd + (j0 + j);
+            const uint32_t* ctr = tile + ((int64_t)(r + 1) * tcols + (j + 1)) * nk;
+            int count = 0;
+            for (int k0 = 0, w = 0; k0 < nk; k0 += 32, ++w) {
+                const int kk = k0 + lane;
+                bool pk = false;
+                if (kk < nk) {
+                    const uint32_t v = ctr[kk];
+                    if (v >= p.thr) {
+                        pk = true;
+                        for (int di = -1; di <= 1 && pk; ++di) {
+                            const int ii = di < 0 ? im : (di > 0 ? ip : i);
+                            const uint32_t* rowp = tile + ((int64_t)(r + 1 + di) * tcols) * nk;
+                            for (int dj = -1; dj <= 1 && pk; ++dj) {
+                                const uint32_t* cp = rowp + (j + 1 + dj) * nk;
+                                for (int dk = -1; dk <= 1; ++dk) {
+                                    const int k2 = kk + dk;
+                                    if (k2 < 0 || k2 >= nk) continue;
+                                    if (ii == i && dj == 0 && dk == 0) continue;  // the cell itself
+                                    const uint32_t u = cp[k2];
+                                    if (u == kAbsent) continue;
+                                    const bool earlier = ii < i || (ii == i && (dj < 0 || (dj == 0 && dk < 0)));
+                                    if (earlier ? !(v > u) : !(v >= u)) {
+                                        pk = false;
+                                        break;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                const unsigned b = __ballot_sync(0xffffffffu, pk);
+                if (lane == 0) {
+                    p.mask[col * nkw + w] = b;
+                    p.wpre[col * nkw + w] = (uint16_t)count;
+                }
+                count += __popc(b);
+            }
+            if (lane == 0) p.npk[col] = count;
+        }
     }
 }
 
@@ -405,72 +501,279 @@ __global__ void scan_down_kernel(const ScanRange r, const int64_t* partial, int 
 }
 
 // ---------------------------------------------------------------------------
-// association: CTA per (event, phi0 row), warps split the d0 columns that hold
-// peaks, each warp sweeps the event's hits in ascending order (32 per step) so
-// that every peak's hit list comes out ascending without a sort.
+// association: the vote's tiling again.  A CTA owns a (phi0, d0) tile of one
+// event, loads the tile's peak bitmasks, marks the kappa bins that lie within
+// `window` of a peak ("near" bits), and streams the event's hits through the
+// same certified binning as the vote.  A hit whose bin is near a peak is
+// appended to each such peak's CSR row through a shared-memory cursor; rows
+// are then put in ascending hit order (most already are) by a warp rank sort.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) assoc_kernel(const AssocParams p) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nkw = (p.K.nk + 31) >> 5;
-    const int64_t nrows = (int64_t)p.n_events * p.K.nphi;
-    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
-        const int e = (int)(row / p.K.nphi);
-        const int i = (int)(row - (int64_t)e * p.K.nphi);
-        const int64_t col0 = row * p.K.nd;
-        // any peaks in this warp's columns?
+constexpr int kSortCap = 1024;  // per-warp shared sort buffer (hit indices)
+constexpr int kQueue = 64;      // per-warp candidate queue (drained at >= 32)
+
+struct AssocSmem {
+    float4* dt;        // [tile_d]
+    uint32_t* mask;    // [tile_cols][nkw] peak bits
+    uint32_t* nearb;   // [tile_cols][nkw] near-peak bits
+    int32_t* lpre;     // [tile_cols][nkw] first local peak slot of the word
+    int64_t* gpre;     // [tile_cols][nkw] first global peak id of the word
+    unsigned long long* wpos;  // [tile_cols * ceil(nk/2)] next CSR write position per local peak
+    uint2* queue;      // [warps][kQueue] (column << 16 | kappa bin, hit)
+    int32_t* sortbuf;  // [warps][kSortCap]
+};
+
+__host__ __device__ inline size_t assoc_smem_bytes(int tile_phi, int tile_d, int nk, int threads) {
+    const size_t cols = (size_t)tile_phi * tile_d, nkw = (nk + 31) / 32;
+    return 16 * (size_t)tile_d + cols * nkw * (4 + 4 + 4 + 8) + cols * ((nk + 1) / 2) * 8 +
+           (size_t)(threads / 32) * (kQueue * 8 + kSortCap * 4) + 64;
+}
+
+// One queued candidate (column c of the tile, kappa bin kb, hit h): append h
+// to every peak within `window` bins of kb.
+__device__ __forceinline__ void assoc_append(const AssocParams& p, const AssocSmem& S, int nkw, int nk, uint2 ent) {
+    const int c = (int)(ent.x >> 16), kb = (int)(ent.x & 0xFFFFu);
+    for (int o = -p.window; o <= p.window; ++o) {
+        const int kk = kb + o;
+        if (kk < 0 || kk >= nk) continue;
+        const int wd = kk >> 5;
+        const uint32_t bits = S.mask[c * nkw + wd];
+        if (!((bits >> (kk & 31)) & 1u)) continue;
+        const int below = __popc(bits & ((1u << (kk & 31)) - 1u));
+        const int64_t pid = S.gpre[c * nkw + wd] + below;
+        if (pid >= p.peak_cap) continue;
+        const unsigned long long pos = atomicAdd(&S.wpos[S.lpre[c * nkw + wd] + below], 1ull);
+        if ((int64_t)pos < p.pair_cap) p.hit_idx[pos] = (int32_t)ent.y;
+    }
+}
+
+// Push this lane's candidate (if any) into the warp queue; drain 32 at a time.
+__device__ __forceinline__ void queue_push(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn, int nkw,
+                                           int nk, bool cand, uint2 ent, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (!m) return;
+    if (cand) q[qn + __popc(m & lanemask_lt())] = ent;
+    qn += __popc(m);
+    if (qn >= 32) {
+        __syncwarp();
+        assoc_append(p, S, nkw, nk, q[qn - 32 + lane]);
+        __syncwarp();
+        qn -= 32;
+    }
+}
+
+__device__ __forceinline__ void queue_drain(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn, int nkw,
+                                            int nk, int lane) {
+    __syncwarp();
+    if (lane < qn) assoc_append(p, S, nkw, nk, q[lane]);
+    __syncwarp();
+    qn = 0;
+}
+
+template <int SPHI, int NK, bool TAIL>
+__device__ __forceinline__ void assoc_one_hit(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn,
+                                              const float* cp, const float* sp, int nj, int nk, int nkw, int64_t h,
+                                              bool valid, int lane) {
+    const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
+    const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
+    const HitFast hf = hit_fast(x, y, p.K);
+    float q_[SPHI];
+#pragma unroll
+    for (int r = 0; r < SPHI; ++r) q_[r] = q_of(x, y, cp[r], sp[r]);
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0, wlo = p.K.wlo, whi = p.K.whi;
+    const unsigned nku = (unsigned)nk;
+    for (int j = 0; j < nj; ++j) {
+        const float4 dt = S.dt[j];
+        const float Rj = hf.r2 + dt.z;
+        bool anyp = false;
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            const int c = j * SPHI + r;
+            unsigned kb;
+            bool vote, pend;
+            stage1(q_[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
+            if (TAIL) {
+                vote &= valid;
+                pend &= valid;
+            }
+            // kb is only meaningful (< n_kappa) when vote; other lanes read word 0
+            const uint32_t nb = S.nearb[c * nkw + (vote ? (kb >> 5) : 0u)];
+            const bool cand = vote && ((nb >> (kb & 31)) & 1u);
+            queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | kb, (unsigned)h), lane);
+            anyp |= pend;
+        }
+        if (__any_sync(0xffffffffu, anyp)) {
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                const int c = j * SPHI + r;
+                unsigned kb;
+                bool vote, pend;
+                stage1(q_[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
+                int kk = -1;
+                if (pend && (!TAIL || valid)) kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                const bool cand = kk >= 0 && ((S.nearb[c * nkw + (kk >> 5)] >> (kk & 31)) & 1u);
+                queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | (unsigned)kk, (unsigned)h),
+                           lane);
+            }
+        }
+    }
+}
+
+// Ascending order of one CSR row (distinct hit indices) by rank sort.
+__device__ void sort_row(int32_t* seg, int n, int32_t* buf, int lane) {
+    if (n <= 1) return;
+    if (n > kSortCap) {  // rare: long rows sorted in place by one lane
+        if (lane == 0) {
+            for (int a = 1; a < n; ++a) {
+                const int32_t v = seg[a];
+                int b = a - 1;
+                while (b >= 0 && seg[b] > v) {
+                    seg[b + 1] = seg[b];
+                    --b;
+                }
+                seg[b + 1] = v;
+            }
+        }
+        __syncwarp();
+        return;
+    }
+    bool unsorted = false;
+    for (int t = lane; t < n; t += 32) {
+        buf[t] = seg[t];
+        if (t + 1 < n) unsorted |= seg[t] > seg[t + 1];
+    }
+    if (!__any_sync(0xffffffffu, unsorted)) return;
+    __syncwarp();
+    for (int t = lane; t < n; t += 32) {
+        const int32_t v = buf[t];
+        int rank = 0;
+        for (int u = 0; u < n; ++u) rank += buf[u] < v;
+        seg[rank] = v;
+    }
+    __syncwarp();
+}
+
+template <int SPHI, int NK>
+__global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, const int tile_d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = NK ? NK : p.K.nk;
+    const int nkw = (nk + 31) >> 5;
+    const int tcols = SPHI * tile_d;
+    const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    AssocSmem S;
+    {
+        unsigned char* ptr = smem_raw;
+        S.dt = reinterpret_cast<float4*>(ptr);
+        ptr += 16 * tile_d;
+        S.gpre = reinterpret_cast<int64_t*>(ptr);
+        ptr += 8 * tcols * nkw;
+        S.wpos = reinterpret_cast<unsigned long long*>(ptr);
+        ptr += 8 * tcols * ((nk + 1) / 2);
+        S.queue = reinterpret_cast<uint2*>(ptr);
+        ptr += 8 * nw * kQueue;
+        S.mask = reinterpret_cast<uint32_t*>(ptr);
+        ptr += 4 * tcols * nkw;
+        S.nearb = reinterpret_cast<uint32_t*>(ptr);
+        ptr += 4 * tcols * nkw;
+        S.lpre = reinterpret_cast<int32_t*>(ptr);
+        ptr += 4 * tcols * nkw;
+        S.sortbuf = reinterpret_cast<int32_t*>(ptr);
+    }
+    uint2* q = S.queue + warp * kQueue;
+    __shared__ int64_t sh[33];
+    const int tiles_phi = (p.K.nphi + SPHI - 1) / SPHI;
+    const int tiles_d = (p.K.nd + tile_d - 1) / tile_d;
+    const int64_t items = (int64_t)p.n_events * tiles_phi * tiles_d;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int e = (int)(item / ((int64_t)tiles_phi * tiles_d));
+        const int t = (int)(item - (int64_t)e * tiles_phi * tiles_d);
+        const int tp = t / tiles_d, td = t - (t / tiles_d) * tiles_d;
+        const int i0 = tp * SPHI, j0 = td * tile_d;
+        const int nj = min(tile_d, p.K.nd - j0);
+        const int nrows = min(SPHI, p.K.nphi - i0);
+        // tile columns c = j * SPHI + r; first-peak ids and local slots
+        int64_t carry = 0;
         bool any = false;
-        for (int j = warp; j < p.K.nd; j += nw)
-            if (p.npk[col0 + j] > 0 && p.colbase[col0 + j] < p.peak_cap) any = true;
-        if (!any) continue;
-        const float c = p.cphi[i], s = p.sphi[i];
+        __syncthreads();
+        for (int c0 = 0; c0 < tcols; c0 += nthr) {
+            const int c = c0 + tid;
+            const int j = c / SPHI, r = c - (c / SPHI) * SPHI;
+            const bool live = c < tcols && j < nj && r < nrows;
+            const int64_t col = live ? ((int64_t)e * p.K.nphi + i0 + r) * p.K.nd + j0 + j : 0;
+            const int n = live ? p.npk[col] : 0;
+            int64_t tot;
+            const int64_t ex = block_exscan64(n, sh, &tot);
+            if (c < tcols) {
+                const int64_t cb = live ? p.colbase[col] : 0;
+                for (int w = 0; w < nkw; ++w) {
+                    const uint32_t m = live ? p.mask[col * nkw + w] : 0u;
+                    const int wp = live ? p.wpre[col * nkw + w] : 0;
+                    S.mask[c * nkw + w] = m;
+                    S.lpre[c * nkw + w] = (int)(carry + ex) + wp;
+                    S.gpre[c * nkw + w] = cb + wp;
+                }
+                any |= n > 0 && cb < p.peak_cap;
+            }
+            carry += tot;
+        }
+        if (!__syncthreads_or(any)) continue;
+        for (int j = tid; j < nj; j += nthr) S.dt[j] = p.dtab[j0 + j];
+        // near bits (a peak within `window`) and each peak's first CSR position
+        for (int v = tid; v < tcols * nkw; v += nthr) {
+            const int c = v / nkw, w = v - (v / nkw) * nkw;
+            const uint32_t* m = S.mask + c * nkw;
+            uint32_t nb = m[w];
+            for (int o = 1; o <= p.window; ++o) {
+                const uint32_t hi_w = w + 1 < nkw ? m[w + 1] : 0u, lo_w = w > 0 ? m[w - 1] : 0u;
+                nb |= (m[w] >> o) | (hi_w << (32 - o)) | (m[w] << o) | (lo_w >> (32 - o));
+            }
+            S.nearb[v] = nb;
+            uint32_t bits = m[w];
+            int below = 0;
+            while (bits) {
+                bits &= bits - 1;
+                const int64_t pid = S.gpre[v] + below;
+                S.wpos[S.lpre[v] + below] =
+                    pid < p.peak_cap ? (unsigned long long)p.peak_offsets[pid] : ~0ull >> 1;
+                ++below;
+            }
+        }
+        float cp[SPHI], sp[SPHI];
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            const int i = r < nrows ? i0 + r : i0;
+            cp[r] = p.cphi[i];
+            sp[r] = p.sphi[i];
+        }
         const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
         const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
-        for (int64_t h0 = hb; h0 < he; h0 += 32) {
-            const int64_t h = h0 + lane;
-            const bool valid = h < he;
-            const float x = valid ? p.x[h] : 0.0f;
-            const float y = valid ? p.y[h] : 0.0f;
-            const HitFast hf = hit_fast(x, y, p.K);
-            const float q = q_of(x, y, c, s);
-            for (int j = warp; j < p.K.nd; j += nw) {
-                const int64_t col = col0 + j;
-                if (p.npk[col] == 0) continue;
-                const int64_t pid0 = p.colbase[col];
-                if (pid0 >= p.peak_cap) continue;
-                const float4 dt = p.dtab[j];
-                int kb = -1;
-                if (valid) {
-                    kb = cell_fast(q, dt.x, dt.y, hf.r2 + dt.z, hf.G, hf.dmin, p.K);
-                    if (kb == -2) kb = cell_slow(x, y, c, s, dt.x, hf.R1, p.K, p.stats);
-                }
-                const uint32_t* mcol = p.mask + col * nkw;
-                unsigned pend = 0;
-                if (kb >= 0) {
-                    for (int o = -p.window; o <= p.window; ++o) {
-                        const int kk = kb + o;
-                        if (kk >= 0 && kk < p.K.nk && ((mcol[kk >> 5] >> (kk & 31)) & 1u))
-                            pend |= 1u << (o + p.window);
-                    }
-                }
-                while (__any_sync(0xffffffffu, pend != 0)) {
-                    const int my = pend ? kb - p.window + (__ffs(pend) - 1) : INT_MAX;
-                    const int kmin = __reduce_min_sync(0xffffffffu, my);
-                    const int rel = kmin - (kb - p.window);
-                    const bool in = pend && rel >= 0 && rel <= 2 * p.window && ((pend >> rel) & 1u);
-                    const unsigned b = __ballot_sync(0xffffffffu, in);
-                    const int64_t pid = pid0 + p.wpre[col * nkw + (kmin >> 5)] +
-                                        __popc(mcol[kmin >> 5] & ((1u << (kmin & 31)) - 1u));
-                    if (pid < p.peak_cap) {
-                        const int64_t base = p.peak_offsets[pid] + p.cursor[pid];
-                        if (in) {
-                            const int64_t pos = base + __popc(b & lanemask_lt());
-                            if (pos < p.pair_cap) p.hit_idx[pos] = (int32_t)h;
-                        }
-                        __syncwarp();
-                        if (lane == 0) p.cursor[pid] += __popc(b);
-                        __syncwarp();
-                    }
-                    if (in) pend &= ~(1u << rel);
+        int qn = 0;
+        __syncthreads();
+        const int64_t nfull = ((he - hb) / nthr) * nthr;
+        for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
+            assoc_one_hit<SPHI, NK, false>(p, S, q, qn, cp, sp, nj, nk, nkw, h, true, lane);
+        {
+            const int64_t h = hb + nfull + tid;
+            if (hb + nfull + (tid - lane) < he)
+                assoc_one_hit<SPHI, NK, true>(p, S, q, qn, cp, sp, nj, nk, nkw, h, h < he, lane);
+        }
+        queue_drain(p, S, q, qn, nkw, nk, lane);
+        __syncthreads();
+        // ascending hit order within every complete row of the tile's peaks
+        int32_t* buf = S.sortbuf + warp * kSortCap;
+        for (int c = warp; c < tcols; c += nw) {
+            for (int w = 0; w < nkw; ++w) {
+                uint32_t m = S.mask[c * nkw + w];
+                int below = 0;
+                while (m) {
+                    m &= m - 1;
+                    const int64_t pid = S.gpre[c * nkw + w] + below;
+                    const int local = S.lpre[c * nkw + w] + below;
+                    ++below;
+                    if (pid >= p.peak_cap) continue;
+                    const int64_t off = p.peak_offsets[pid];
+                    const int64_t end = (int64_t)S.wpos[local];
+                    if (end > p.pair_cap) continue;  // row cut by the output cap
+                    sort_row(p.hit_idx + off, (int)(end - off), buf, lane);
                 }
             }
         }
@@ -508,24 +811,41 @@ int vote_smem_bytes(int tile_phi, int tile_d, int nk) {
     return 16 * tile_d + 4 * tile_phi * tile_d * nk;
 }
 
+
 template <int S>
 static cudaError_t prep_one(int smem) {
     return cudaFuncSetAttribute(vote_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-template <int S>
-static cudaError_t occ_one(int threads, int smem, int* blocks) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, vote_kernel<S>, threads, smem);
+template <int S, int N>
+static void* vote_fn() {
+    return reinterpret_cast<void*>(vote_kernel<S, N>);
 }
 
-cudaError_t vote_occupancy(int tile_phi, int threads, int smem, int* blocks) {
-    switch (tile_phi) {
-        case 1: return occ_one<1>(threads, smem, blocks);
-        case 2: return occ_one<2>(threads, smem, blocks);
-        case 4: return occ_one<4>(threads, smem, blocks);
-        case 8: return occ_one<8>(threads, smem, blocks);
+// kernel instance for (tile_phi, n_kappa): compile-time n_kappa for the common widths
+static void* vote_instance(int tile_phi, int nk) {
+#define HT_VOTE_NK(S)                         \
+    switch (nk) {                             \
+        case 64: return vote_fn<S, 64>();     \
+        case 128: return vote_fn<S, 128>();   \
+        case 256: return vote_fn<S, 256>();   \
+        case 512: return vote_fn<S, 512>();   \
+        default: return vote_fn<S, 0>();      \
     }
-    return cudaErrorInvalidValue;
+    switch (tile_phi) {
+        case 1: HT_VOTE_NK(1)
+        case 2: HT_VOTE_NK(2)
+        case 4: HT_VOTE_NK(4)
+        case 8: HT_VOTE_NK(8)
+    }
+#undef HT_VOTE_NK
+    return nullptr;
+}
+
+cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks) {
+    void* f = vote_instance(tile_phi, nk);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
 }
 
 cudaError_t launch_finalize(int64_t* scal, cudaStream_t s) {
@@ -533,26 +853,18 @@ cudaError_t launch_finalize(int64_t* scal, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t vote_prepare(int tile_phi, int smem) {
-    switch (tile_phi) {
-        case 1: return prep_one<1>(smem);
-        case 2: return prep_one<2>(smem);
-        case 4: return prep_one<4>(smem);
-        case 8: return prep_one<8>(smem);
-    }
-    return cudaErrorInvalidValue;
+cudaError_t vote_prepare(int tile_phi, int nk, int smem) {
+    void* f = vote_instance(tile_phi, nk);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    switch (tile_phi) {
-        case 1: vote_kernel<1><<<grid, threads, smem, s>>>(p); break;
-        case 2: vote_kernel<2><<<grid, threads, smem, s>>>(p); break;
-        case 4: vote_kernel<4><<<grid, threads, smem, s>>>(p); break;
-        case 8: vote_kernel<8><<<grid, threads, smem, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    void* f = vote_instance(tile_phi, p.K.nk);
+    if (!f) return cudaErrorInvalidValue;
+    void* args[] = {const_cast<VoteParams*>(&p)};
+    return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer, int64_t n_hits,
@@ -578,10 +890,35 @@ static int warp_grid(int64_t ncols, int threads) {
     return blocks < 1 ? 1 : (int)blocks;
 }
 
+// detect tile: R interior rows x TD interior columns, halo included, ~96 KB
+void detect_tile(int nphi, int nd, int nk, int* R, int* TD) {
+    const int64_t budget = 96 * 1024 / 4;  // words
+    int td = nd;
+    while (td > 1 && (int64_t)3 * (td + 2) * nk > budget) td = (td + 1) / 2;
+    int r = (int)(budget / ((int64_t)(td + 2) * nk)) - 2;
+    r = std::max(1, std::min(r, nphi));
+    *R = r;
+    *TD = td;
+}
+
+size_t detect_smem(int nphi, int nd, int nk) {
+    int R, TD;
+    detect_tile(nphi, nd, nk, &R, &TD);
+    return (size_t)(R + 2) * (TD + 2) * nk * 4;
+}
+
+cudaError_t detect_prepare(int nphi, int nd, int nk) {
+    return cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)detect_smem(nphi, nd, nk));
+}
+
 cudaError_t launch_detect(const PeakParams& p, cudaStream_t s) {
-    const int64_t ncols = (int64_t)p.n_events * p.nphi * p.nd;
-    if (ncols == 0) return cudaSuccess;
-    detect_kernel<<<warp_grid(ncols, 256), 256, 0, s>>>(p);
+    if ((int64_t)p.n_events * p.nphi * p.nd == 0) return cudaSuccess;
+    int R, TD;
+    detect_tile(p.nphi, p.nd, p.nk, &R, &TD);
+    const int64_t items = (int64_t)p.n_events * ((p.nphi + R - 1) / R) * ((p.nd + TD - 1) / TD);
+    const int grid = (int)std::min<int64_t>(items, 152 * 8);
+    detect_kernel<<<grid, 256, detect_smem(p.nphi, p.nd, p.nk), s>>>(p, R, TD);
     return cudaGetLastError();
 }
 
@@ -605,12 +942,51 @@ cudaError_t launch_scan(const ScanRange& r, int64_t* scratch, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_assoc(const AssocParams& p, cudaStream_t s) {
-    const int64_t nrows = (int64_t)p.n_events * p.K.nphi;
-    if (nrows == 0) return cudaSuccess;
-    int64_t grid = nrows < (1 << 20) ? nrows : (1 << 20);
-    assoc_kernel<<<(int)grid, 128, 0, s>>>(p);
-    return cudaGetLastError();
+template <int S, int N>
+static void* assoc_fn() {
+    return reinterpret_cast<void*>(assoc_kernel<S, N>);
+}
+
+static void* assoc_instance(int tile_phi, int nk) {
+#define HT_ASSOC_NK(S)                         \
+    switch (nk) {                              \
+        case 64: return assoc_fn<S, 64>();     \
+        case 128: return assoc_fn<S, 128>();   \
+        case 256: return assoc_fn<S, 256>();   \
+        case 512: return assoc_fn<S, 512>();   \
+        default: return assoc_fn<S, 0>();      \
+    }
+    switch (tile_phi) {
+        case 1: HT_ASSOC_NK(1)
+        case 2: HT_ASSOC_NK(2)
+        case 4: HT_ASSOC_NK(4)
+        case 8: HT_ASSOC_NK(8)
+    }
+#undef HT_ASSOC_NK
+    return nullptr;
+}
+
+size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads) {
+    return assoc_smem_bytes(tile_phi, tile_d, nk, threads);
+}
+
+cudaError_t assoc_prepare(int tile_phi, int nk, int smem) {
+    void* f = assoc_instance(tile_phi, nk);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int tile_d, int threads, cudaStream_t s) {
+    if ((int64_t)p.n_events * p.K.nphi == 0) return cudaSuccess;
+    void* f = assoc_instance(tile_phi, p.K.nk);
+    if (!f) return cudaErrorInvalidValue;
+    const int tiles = ((p.K.nphi + tile_phi - 1) / tile_phi) * ((p.K.nd + tile_d - 1) / tile_d);
+    const int64_t items = (int64_t)p.n_events * tiles;
+    const int grid = (int)std::min<int64_t>(items, 152 * 32);
+    const int smem = (int)assoc_smem_bytes(tile_phi, tile_d, p.K.nk, threads);
+    int td = tile_d;
+    void* args[] = {const_cast<AssocParams*>(&p), &td};
+    return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s) {

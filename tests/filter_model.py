@@ -31,14 +31,14 @@ def consts(grid, d0):
     dabs = float(np.max(np.abs(np.asarray(d0, np.float64))))
     V0 = max(abs(Hd), abs(nk - Hd))
     ev = ER + 4 * U + 1 / 63
-    m = math.ceil(2 * (ev * (nk + abs(Hd)) + 0.26) / (1 - ev)) + 1
+    m = math.ceil(2 * (ev * (nk + abs(Hd)) + 0.3) / (1 - ev)) + 1
     Vmax = V0 + m
     S2 = float(F(2 * scale))
     K = dict(nk=nk, S2=F(2 * scale), H=F(Hd), dabs=F(dabs), wlo=F(-m), whi=F(nk + m),
              T0=F(2 * ((ER + 3 * U) * Vmax + U * (abs(Hd) + 2 * (nk + m)) + U)),
              cG1=F(2 * (64 / 63) * 4.03 * U * Vmax * (1 + ER) * (1 + ER + 4 * U)),
              cG2=F(2 * 1.01 * S2 * U * (1 + ER)),
-             cD1=F(64 * 4.03 * U), cD2=F(4.1 * 1.01 * S2 * U * (1 + ER)))
+             cD1=F(64 * 4.03 * U), cD2=F(3.6 * 1.01 * S2 * U * (1 + ER)))
     V2 = V0 + 2
     K.update(S2hi=F(2 * scale), H_hi=F(Hd))
     K.update(S2lo=F(2 * scale - float(K["S2hi"])), H_lo=F(Hd - float(K["H_hi"])),
@@ -57,8 +57,9 @@ def stage1(x, y, c, s, d, K, rcp_err=0.0):
         R1 = r + K["dabs"]
         P1 = fma(F(3.02), r, F(1.01) * K["dabs"])
         R1s = R1 * R1
-        G = fma(K["cG1"], R1s, K["cG2"] * P1)
         dmin = np.maximum(K["cD1"] * R1s, K["cD2"] * P1)
+        # G >= 0.55 dmin: a cell with den <= dmin gets tau > 1/2 and is never certified
+        G = np.maximum(fma(K["cG1"], R1s, K["cG2"] * P1), F(0.55) * dmin)
         q = fma(y, c, -(x * s))
         Rj = r2 + d * d
         a = q - d
@@ -66,15 +67,19 @@ def stage1(x, y, c, s, d, K, rcp_err=0.0):
         rc = (1.0 / den.astype(np.float64) * (1.0 + rcp_err)).astype(F)
         t = a * rc
         w = fma(t, K["S2"], K["H"])
-        tau = fma(G, rc, K["T0"])
+        tau = fma(G, np.abs(rc), K["T0"])
         lo, hi = w - tau, w + tau
         flo, fhi = np.floor(lo), np.floor(hi)
         denok = den > dmin
-        same = denok & (flo == fhi) & np.isfinite(lo) & (np.abs(lo) < 2 ** 22)
+        same = (flo == fhi) & np.isfinite(lo) & (np.abs(lo) < 2 ** 22)
+        # the implicit den test: a certified cell always has den > dmin
+        assert not np.any(same & ~denok), "certified a cell below den_min"
         k = np.where(same, flo, 0).astype(np.int64)
         out = np.full(x.shape, -2, np.int64)
         out[same] = np.where((k[same] >= 0) & (k[same] < K["nk"]), k[same], -1)
-        far = denok & ~same & ~((w > K["wlo"]) & (w < K["whi"]))
+        # uncertified cells go to stage 2 unless den > den_min and w lies outside
+        # (-m, n_kappa + m), which proves them out of range
+        far = ~same & denok & ~((w > K["wlo"]) & (w < K["whi"]))
         out[far] = -1
     return out
 
