@@ -313,6 +313,15 @@ def run_gpu(args):
         e2e = {"value": world * n_events / float(np.mean(et)), "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et))}
 
+    # ---- serving: continuous batching at two offered loads (rank 0, N=1)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        from paper_1311_2769_gb300 import serve
+        try:
+            serving = serve.measure([50000.0, 200000.0], n_events=3000)
+        except Exception as e:  # report, do not hide, a failing loop
+            serving = {"error": f"{type(e).__name__}: {e}"}
+
     # ---- roofline of the dominant kernel (vote): issue-bound ALU work
     peaks, peak_src = _peaks()
     clk = clocks.summary()
@@ -347,6 +356,7 @@ def run_gpu(args):
         "clocks": clk,
         "gpu_launches": int(launches) * args.steps,
         "e2e": e2e,
+        "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, batch)
@@ -365,6 +375,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--events", type=int, default=None, help="events per batch (default: the full 4096)")
     ap.add_argument("--tile", default="", help="vote tile 'phi,d0,threads' instead of autotuning")
     ap.add_argument("--no-extras", action="store_true",

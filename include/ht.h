@@ -125,6 +125,8 @@ typedef struct {
 #define HT_OPT_USE_GRAPH 7         /* 1 = replay the batched step as a CUDA graph (default 1) */
 #define HT_OPT_PHASE_TIMING 8      /* 1 = time vote / peaks+association with device events */
 #define HT_OPT_LAUNCHES 9          /* read-only: kernels launched by the last ht_process */
+#define HT_OPT_ATILE_PHI 10        /* phi0 rows per association tile: 1, 2, 4 or 8 (0 = auto) */
+#define HT_OPT_ATILE_D0 11         /* d0 columns per association tile (0 = auto) */
 
 #define HT_MODE_BATCHED 0 /* one persistent launch per kernel over all (event, tile) items */
 #define HT_MODE_PLAIN 1   /* one launch sequence per event */
@@ -186,7 +188,10 @@ int ht_get_tables(ht_ctx *ctx, float *cos_phi, float *sin_phi, float *d0);
 int ht_sync(ht_ctx *ctx);
 
 /* Time the vote for a few tile shapes on `hits` and keep the fastest
- * (HT_OPT_TILE_PHI / HT_OPT_TILE_D0 / HT_OPT_THREADS).  Synchronous. */
+ * (HT_OPT_TILE_PHI / HT_OPT_TILE_D0 / HT_OPT_THREADS), then time the peaks +
+ * association phase for a few association tiles (HT_OPT_ATILE_PHI /
+ * HT_OPT_ATILE_D0, measured at threshold 9 and window 1).  Synchronous;
+ * the sample must fit the accumulator budget. */
 int ht_autotune(ht_ctx *ctx, const ht_hits *hits, void *stream);
 
 /* Device time of the last single-wave ht_process (needs HT_OPT_PHASE_TIMING=1,

@@ -74,13 +74,14 @@ struct ht_ctx {
     // options
     int mode = HT_MODE_BATCHED;
     int tile_phi = 0, tile_d = 0, threads = 0;
+    int atile_phi = 0, atile_d = 0;  // association tile (0 = auto)
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
 
     // resolved tile configuration
     int r_tile_phi = 1, r_tile_d = 1, r_threads = 256, r_smem = 0, r_blocks_per_sm = 1;
-    int a_tile_d = 1, a_threads = 256, a_smem = 0;  // association tile (same phi rows)
+    int a_tile_phi = 1, a_tile_d = 1, a_threads = 256, a_smem = 0;  // association tile
 
     int gen = 0;  // buffer generation (graph invalidation)
     DBuf<float> sx, sy;
@@ -257,14 +258,17 @@ int resolve_tiles(ht_ctx* ctx) {
     ctx->r_threads = thr;
     ctx->r_smem = smem;
     ctx->r_blocks_per_sm = per_sm;
-    // association tile: same phi rows, d0 width halved until its metadata,
-    // cursors and sort buffers fit in 200 KB of shared memory
-    int atd = td;
+    // association tile: its own phi rows and d0 width (default 4 x 16), the
+    // width halved until metadata, write cursors, queues and sort buffers fit
+    // in 200 KB of shared memory
+    const int atp = ctx->atile_phi > 0 ? std::min(ctx->atile_phi, 8) : std::min(4, ctx->grid.n_phi >= 4 ? 4 : 1);
+    int atd = ctx->atile_d > 0 ? std::min(ctx->atile_d, nd) : std::min(nd, 16);
     const int athr = std::min(thr, 256);
-    while (atd > 1 && assoc_smem(tp, atd, nk, athr) > 200 * 1024) atd = (atd + 1) / 2;
-    const int asmem = (int)assoc_smem(tp, atd, nk, athr);
+    while (atd > 1 && assoc_smem(atp, atd, nk, athr) > 200 * 1024) atd = (atd + 1) / 2;
+    const int asmem = (int)assoc_smem(atp, atd, nk, athr);
     if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association tile does not fit shared memory");
-    CU(assoc_prepare(tp, nk, asmem));
+    CU(assoc_prepare(atp, nk, asmem));
+    ctx->a_tile_phi = atp;
     ctx->a_tile_d = atd;
     ctx->a_threads = athr;
     ctx->a_smem = asmem;
@@ -455,7 +459,7 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, i
     a.dtab = ctx->d_dtab;
     a.K = ctx->K;
     a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
-    CU(launch_assoc(a, ctx->r_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
+    CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
     return HT_OK;
 }
 
@@ -576,7 +580,8 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
     std::vector<float4> dt(grid->n_d0);
     for (int j = 0; j < grid->n_d0; ++j) {
         const float d = ctx->h_d0[j];
-        dt[j] = make_float4(d, d + d, d * d, 0.0f);
+        // (d0, 2 d0, d0^2, d0 * S2): the last is the kappa-scaled d0 of stage 1
+        dt[j] = make_float4(d, d + d, d * d, (float)((double)d * (double)ctx->K.S2));
     }
     int st = HT_OK;
     auto bad = [&](cudaError_t e) {
@@ -670,6 +675,15 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             break;
         case HT_OPT_COUNT_STAGES: ctx->count_stages = value != 0; break;
         case HT_OPT_USE_GRAPH: ctx->use_graph = value != 0; break;
+        case HT_OPT_ATILE_PHI:
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+                return fail(ctx, HT_ERR_INVALID_ARG, "association tile_phi must be 0, 1, 2, 4 or 8");
+            ctx->atile_phi = (int)value;
+            break;
+        case HT_OPT_ATILE_D0:
+            if (value < 0 || value > ctx->grid.n_d0) return fail(ctx, HT_ERR_INVALID_ARG, "association tile_d0 out of range");
+            ctx->atile_d = (int)value;
+            break;
         case HT_OPT_PHASE_TIMING:
             if (value && !ctx->tev[0])
                 for (auto& e : ctx->tev) CU(cudaEventCreate(&e));
@@ -678,7 +692,8 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
     ctx->gvalid = false;
-    if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS) {
+    if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS || key == HT_OPT_ATILE_PHI ||
+        key == HT_OPT_ATILE_D0) {
         int st = resolve_tiles(ctx);
         if (st) return st;
     }
@@ -696,6 +711,8 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_COUNT_STAGES: *value = ctx->count_stages; break;
         case HT_OPT_USE_GRAPH: *value = ctx->use_graph; break;
         case HT_OPT_PHASE_TIMING: *value = ctx->timing; break;
+        case HT_OPT_ATILE_PHI: *value = ctx->a_tile_phi; break;
+        case HT_OPT_ATILE_D0: *value = ctx->a_tile_d; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
@@ -810,7 +827,7 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     a.dtab = ctx->d_dtab;
     a.K = ctx->K;
     a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
-    CU(launch_assoc(a, ctx->r_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
+    CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
     CU(cudaMemcpyAsync(peak_offsets, ctx->peakoff.p, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     const int64_t ncopy = std::min(total, cap);
     if (ncopy > 0) CU(cudaMemcpyAsync(hit_idx, ctx->hitidx.p, ncopy * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1030,9 +1047,9 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (bp == 0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
         ctx->tile_phi = save_p;
         ctx->tile_d = save_d;
         ctx->threads = save_t;
@@ -1042,6 +1059,59 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     ctx->tile_phi = bp;
     ctx->tile_d = bd;
     ctx->threads = bt;
+    st = resolve_tiles(ctx);
+    if (st) return st;
+    // association tile, timed on the peaks + association phase of one wave
+    // (threshold 9, window 1: the batch workload's reading)
+    {
+        DBuf<ht_peak> pk;
+        DBuf<int64_t> po;
+        DBuf<int32_t> hi;
+        const int64_t pcap = std::min<int64_t>(ctx->cells * ctx->c_events / 8 + 1024, 1LL << 27);
+        const int64_t qcap = std::min<int64_t>(pcap * 64, 1LL << 31);
+        if (pk.ensure(pcap, nullptr) == cudaSuccess && po.ensure(pcap + 1, nullptr) == cudaSuccess &&
+            hi.ensure(qcap, nullptr) == cudaSuccess && ctx->paircnt.ensure(pcap, &ctx->gen) == cudaSuccess) {
+            const int save_ap = ctx->atile_phi, save_ad = ctx->atile_d;
+            float abest = 1e30f;
+            int ap_best = 0, ad_best = 0;
+            const int32_t epw = events_per_wave(ctx, ctx->c_events);
+            for (int ap : {1, 2, 4, 8}) {
+                if (ap > ctx->grid.n_phi) continue;
+                for (int ad : {nd, 32, 16, 8}) {
+                    if (ad > nd) continue;
+                    ctx->atile_phi = ap;
+                    ctx->atile_d = ad;
+                    if (resolve_tiles(ctx)) continue;
+                    if (ctx->a_tile_d != ad) continue;  // did not fit
+                    const bool timing = ctx->timing;
+                    if (!ctx->tev[0])
+                        for (auto& ev : ctx->tev) CU(cudaEventCreate(&ev));
+                    ctx->timing = true;
+                    process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, epw, s);  // warm
+                    process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, epw, s);
+                    CU(cudaStreamSynchronize(s));
+                    ctx->timing = timing;
+                    float ms = 0;
+                    if (cudaEventElapsedTime(&ms, ctx->tev[1], ctx->tev[2]) != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    if (ms < abest) {
+                        abest = ms;
+                        ap_best = ap;
+                        ad_best = ad;
+                    }
+                }
+            }
+            ctx->atile_phi = ap_best ? ap_best : save_ap;
+            ctx->atile_d = ap_best ? ad_best : save_ad;
+        }
+        pk.release();
+        po.release();
+        hi.release();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     ctx->gvalid = false;
     ctx->have_votes = ctx->have_peaks = false;
     return resolve_tiles(ctx);

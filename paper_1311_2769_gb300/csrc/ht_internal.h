@@ -24,7 +24,7 @@ struct VoteParams {
     int64_t cells;
     const float* cphi;
     const float* sphi;
-    const float4* dtab;    // (d0_j, 2 d0_j, d0_j^2, 0)
+    const float4* dtab;    // (d0_j, 2 d0_j, d0_j^2, d0_j * S2)
     KConsts K;
     unsigned long long* stats;
 };

@@ -34,7 +34,7 @@ struct KConsts {
     float S2;       // float(2 * scale), scale = n_kappa / (kappa_max - kappa_min)
     float H;        // float(-kappa_min * scale)
     float T0;       // constant part of tau
-    float cG1, cG2; // tau = T0 + (cG1 R1^2 + cG2 P1) * rcp(den), P1 = 3.02 r + 1.01 dabs
+    float cG1, cG2; // tau = T0 + (cG1 R1^2 + cG2 P1) * |rcp(den)|, P1 = 4.02 r + 2.02 dabs
     float cD1, cD2; // den_min = max(cD1 R1^2, cD2 P1): below it the bound is not used
     float wlo, whi; // w outside (wlo, whi) = (-m, n_kappa + m) is out of range for sure
     float dabs;
@@ -60,54 +60,49 @@ __device__ __forceinline__ float rcp_approx(float x) {
 //   per (hit,j)  Rj = fl(r2 + fl(d*d))                    |Rj - R*|  <= 3.02 u r^2 + 2.01 u d^2
 // Per cell:
 //   a   = fl(q - d)                                       |a - a*|   <= u (3.02 r + 1.01 |d|)
+//   (the kernels fold S2 in: a' = fl(fl(q S2) - fl(d S2)), |a' - S2 a*| <= S2 u (4.02 r + 2.02 |d|))
 //   den = fl(fma(-2d, q, Rj))                             |den-den*| <= E = 4.03 u R1^2
 //   w   = fl(fma(fl(a * rcp(den)), S2, H))
 // With den > den_min >= 64 E the relative error of den is <= 1/64, and for a
 // cell whose w lies in (-m, n_kappa + m) (so |v| <= V):
 //   |w - w*| <= (e_r + 3u) V + u(|H| + 2 (n_kappa + m)) + u     (constant: T0)
-//             + (64/63) E V / den + 1.01 S2 u (3.02 r + 1.01 |d|) / den   (per-hit: G)
+//             + (64/63) E V / den + 1.01 S2 u (4.02 r + 2.02 |d|) / den   (per-hit: G)
 // and w* (the exact real value) is within ~1e-11 bins of the binary64 w.
 // A cell whose w lies outside (-m, n_kappa + m) is out of range in binary64
 // too: m is chosen on the host so that m (1 - e_v) exceeds e_v (n_kappa + |H|) + 0.3, where
 // e_v <= e_r + 4u + 1/63 bounds the relative error of v and 0.3 bounds the
 // absolute part (den >= den_min also caps the a-error term at 0.28 bins).
-// Returns k >= 0 (vote), -1 (no vote) or -2 (undecided: use cell_slow).
-__device__ __forceinline__ int cell_fast(float q, float dj, float d2j, float Rj, float G, float dmin,
-                                         const KConsts& K) {
-    const float a = q - dj;
-    const float den = fmaf(-d2j, q, Rj);
-    const float rc = rcp_approx(den);
-    const float t = a * rc;
-    const float w = fmaf(t, K.S2, K.H);
-    const float tau = fmaf(G, fabsf(rc), K.T0);
-    // floor(w -+ tau) by round-down addition of 1.5 * 2^23 (exact for |.| < 2^22)
-    const float flo = __fadd_rd(w - tau, 12582912.0f);
-    const float fhi = __fadd_rd(w + tau, 12582912.0f);
-    const int k = __float_as_int(flo) - 0x4B400000;
-    const bool denok = den > dmin;
-    if (denok && flo == fhi) return ((unsigned)k < (unsigned)K.nk) ? k : -1;
-    if (denok && !(w > K.wlo && w < K.whi)) return -1;
-    return -2;
+// Stage 1 as the tile kernels evaluate it, with the kappa scale folded into
+// the operands: qs = fl(q * S2) per (hit, row) and ds = fl(d * S2) from the
+// table, a' = fl(qs - ds), w = fl(fma(a', rcp(den), H)).  Relative to the
+// unfolded form the a-error becomes S2 u (4.02 r + 2.02 |d|) (P1 below) and
+// the product t disappears; the bound keeps the same shape.
+// stage1_fast: the certified bin candidate; decided iff flo == fhi, then kb
+// is the bin (a vote iff kb < n_kappa).  The den > den_min test is implicit
+// (G >= 0.55 den_min makes tau > 1/2 below it).
+struct S1 {
+    float flo, fhi, w, den;
+    unsigned kb;
+};
+
+__device__ __forceinline__ S1 stage1_fast(float qs, float q, float4 dt, float Rj, float G, float H, float T0) {
+    S1 o;
+    const float a = qs - dt.w;
+    o.den = fmaf(-dt.y, q, Rj);
+    const float rc = rcp_approx(o.den);
+    o.w = fmaf(a, rc, H);
+    const float tau = fmaf(G, fabsf(rc), T0);
+    o.flo = __fadd_rd(o.w - tau, 12582912.0f);
+    o.fhi = __fadd_rd(o.w + tau, 12582912.0f);
+    o.kb = __float_as_uint(o.flo) - 0x4B400000u;
+    return o;
 }
 
-// Stage 1 in the form the tile kernels use: `vote` when the certified bin
-// kb lies in [0, n_kappa), `pend` when stage 2 must decide.  The den > den_min
-// test is implicit for certification (G >= 0.55 den_min makes tau > 1/2
-// below it) and explicit only for the window shortcut, which needs it.
-__device__ __forceinline__ void stage1(float q, float4 dt, float Rj, float G, float dmin, float S2, float H,
-                                       float T0, float wlo, float whi, unsigned nk, unsigned& kb, bool& vote,
-                                       bool& pend) {
-    const float a = q - dt.x;
-    const float den = fmaf(-dt.y, q, Rj);
-    const float rc = rcp_approx(den);
-    const float w = fmaf(a * rc, S2, H);
-    const float tau = fmaf(G, fabsf(rc), T0);
-    const float flo = __fadd_rd(w - tau, 12582912.0f);
-    const float fhi = __fadd_rd(w + tau, 12582912.0f);
-    kb = __float_as_uint(flo) - 0x4B400000u;
-    const bool decided = flo == fhi;
-    vote = decided & (kb < nk);
-    pend = !decided & (!(den > dmin) | ((w > wlo) & (w < whi)));
+// For a cell stage1_fast did not decide: does it need stage 2?  Not when
+// den > den_min (the bound holds) and w lies outside (-m, n_kappa + m),
+// which proves it out of range.
+__device__ __forceinline__ bool stage1_pending(const S1& o, float dmin, float wlo, float whi) {
+    return !(o.den > dmin) || ((o.w > wlo) & (o.w < whi));
 }
 
 // ---- stage 2: double-float ---------------------------------------------
@@ -232,7 +227,7 @@ __device__ __forceinline__ HitFast hit_fast(float x, float y, const KConsts& K) 
     h.r2 = fmaf(x, x, __fmul_rn(y, y));
     const float r = sqrtf(h.r2);
     h.R1 = r + K.dabs;
-    const float P1 = fmaf(3.02f, r, 1.01f * K.dabs);
+    const float P1 = fmaf(4.02f, r, 2.02f * K.dabs);
     const float R1s = h.R1 * h.R1;
     h.dmin = fmaxf(K.cD1 * R1s, K.cD2 * P1);
     // G >= 0.55 dmin: a cell with den <= dmin (or den <= 0, via |rcp|) gets

@@ -41,11 +41,21 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Predicated shared reduction: no branch around the atomic in the hot loop.
-__device__ __forceinline__ void red_shared_if(uint32_t addr, bool pred) {
+// Shared reduction when stage 1 certified a bin in range (flo == fhi and
+// kb < n_kappa [and the lane holds a hit]); the test lives in the same PTX
+// block so no branch or predicate round trip surrounds the atomic.
+__device__ __forceinline__ void red_if_vote(uint32_t addr, float flo, float fhi, unsigned kb, unsigned nk) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(addr),
-        "r"((unsigned)pred));
+        "{\n\t.reg .pred p;\n\tsetp.eq.f32 p, %1, %2;\n\tsetp.lt.and.u32 p, %3, %4, p;\n\t"
+        "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(addr),
+        "f"(flo), "f"(fhi), "r"(kb), "r"(nk));
+}
+__device__ __forceinline__ void red_if_vote(uint32_t addr, float flo, float fhi, unsigned kb, unsigned nk,
+                                            bool valid) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.eq.f32 p, %1, %2;\n\tsetp.lt.and.u32 p, %3, %4, p;\n\t"
+        "setp.ne.and.u32 p, %5, 0, p;\n\t@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(addr),
+        "f"(flo), "f"(fhi), "r"(kb), "r"(nk), "r"((unsigned)valid));
 }
 
 struct TileHit {
@@ -62,36 +72,37 @@ __device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* c
     const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
     const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
     const HitFast hf = hit_fast(x, y, p.K);
-    float q[SPHI];
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    float q[SPHI], qs[SPHI];
 #pragma unroll
-    for (int r = 0; r < SPHI; ++r) q[r] = q_of(x, y, cp[r], sp[r]);
-    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0, wlo = p.K.wlo, whi = p.K.whi;
+    for (int r = 0; r < SPHI; ++r) {
+        q[r] = q_of(x, y, cp[r], sp[r]);
+        qs[r] = q[r] * S2;
+    }
     const unsigned nku = (unsigned)nk;
     const int col_words = SPHI * nk;
     uint32_t col_sh = acc_sh;
     for (int j = 0; j < nj; ++j, col_sh += 4u * col_words) {
         const float4 dt = dt_s[j];
         const float Rj = hf.r2 + dt.z;
-        bool anyp = false;
+        bool und = false;
 #pragma unroll
         for (int r = 0; r < SPHI; ++r) {
-            unsigned kb;
-            bool vote, pend;
-            stage1(q[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
+            const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+            const uint32_t addr = col_sh + 4u * ((unsigned)(r * nk) + o.kb);
             if (TAIL) {
-                vote &= valid;
-                pend &= valid;
+                red_if_vote(addr, o.flo, o.fhi, o.kb, nku, valid);
+                und |= (o.flo != o.fhi) & valid;
+            } else {
+                red_if_vote(addr, o.flo, o.fhi, o.kb, nku);
+                und |= o.flo != o.fhi;
             }
-            red_shared_if(col_sh + 4u * ((unsigned)(r * nk) + kb), vote);
-            anyp |= pend;
         }
-        if (__any_sync(0xffffffffu, anyp)) {
+        if (__any_sync(0xffffffffu, und)) {
 #pragma unroll
             for (int r = 0; r < SPHI; ++r) {
-                unsigned kb;
-                bool vote, pend;
-                stage1(q[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
-                if (pend && (!TAIL || valid)) {
+                const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+                if ((o.flo != o.fhi) && (!TAIL || valid) && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi)) {
                     const int kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
                     if (kk >= 0) atomicAdd(acc_s + j * col_words + r * nk + kk, 1u);
                 }
@@ -247,7 +258,7 @@ __global__ void order_kernel(const int32_t* offs, int32_t event0, int32_t n_even
 // with the linear-order tie rule, leaving at the first failure.
 constexpr uint32_t kAbsent = 0xFFFFFFFFu;
 
-__global__ void __launch_bounds__(256) detect_kernel(const PeakParams p, const int R, const int TD) {
+__global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const int R, const int TD) {
     extern __shared__ __align__(16) uint32_t tile[];
     const int nk = p.nk, nkw = p.nkw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -520,12 +531,13 @@ struct AssocSmem {
     unsigned long long* wpos;  // [tile_cols * ceil(nk/2)] next CSR write position per local peak
     uint2* queue;      // [warps][kQueue] (column << 16 | kappa bin, hit)
     int32_t* sortbuf;  // [warps][kSortCap]
+    int32_t* active;   // [tile_d] d0 columns of the tile holding any peak
 };
 
 __host__ __device__ inline size_t assoc_smem_bytes(int tile_phi, int tile_d, int nk, int threads) {
     const size_t cols = (size_t)tile_phi * tile_d, nkw = (nk + 31) / 32;
     return 16 * (size_t)tile_d + cols * nkw * (4 + 4 + 4 + 8) + cols * ((nk + 1) / 2) * 8 +
-           (size_t)(threads / 32) * (kQueue * 8 + kSortCap * 4) + 64;
+           (size_t)(threads / 32) * (kQueue * 8 + kSortCap * 4) + 4 * (size_t)tile_d + 64;
 }
 
 // One queued candidate (column c of the tile, kappa bin kb, hit h): append h
@@ -571,45 +583,44 @@ __device__ __forceinline__ void queue_drain(const AssocParams& p, const AssocSme
 
 template <int SPHI, int NK, bool TAIL>
 __device__ __forceinline__ void assoc_one_hit(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn,
-                                              const float* cp, const float* sp, int nj, int nk, int nkw, int64_t h,
-                                              bool valid, int lane) {
+                                              const float* cp, const float* sp, int n_active, int nk, int nkw,
+                                              int64_t h, bool valid, int lane) {
     const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
     const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
     const HitFast hf = hit_fast(x, y, p.K);
-    float q_[SPHI];
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    float q_[SPHI], qs[SPHI];
 #pragma unroll
-    for (int r = 0; r < SPHI; ++r) q_[r] = q_of(x, y, cp[r], sp[r]);
-    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0, wlo = p.K.wlo, whi = p.K.whi;
+    for (int r = 0; r < SPHI; ++r) {
+        q_[r] = q_of(x, y, cp[r], sp[r]);
+        qs[r] = q_[r] * S2;
+    }
     const unsigned nku = (unsigned)nk;
-    for (int j = 0; j < nj; ++j) {
+    for (int ja = 0; ja < n_active; ++ja) {
+        const int j = S.active[ja];
         const float4 dt = S.dt[j];
         const float Rj = hf.r2 + dt.z;
-        bool anyp = false;
+        bool und = false;
 #pragma unroll
         for (int r = 0; r < SPHI; ++r) {
             const int c = j * SPHI + r;
-            unsigned kb;
-            bool vote, pend;
-            stage1(q_[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
-            if (TAIL) {
-                vote &= valid;
-                pend &= valid;
-            }
+            const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+            bool vote = (o.flo == o.fhi) & (o.kb < nku);
+            if (TAIL) vote &= valid;
             // kb is only meaningful (< n_kappa) when vote; other lanes read word 0
-            const uint32_t nb = S.nearb[c * nkw + (vote ? (kb >> 5) : 0u)];
-            const bool cand = vote && ((nb >> (kb & 31)) & 1u);
-            queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | kb, (unsigned)h), lane);
-            anyp |= pend;
+            const uint32_t nb = S.nearb[c * nkw + (vote ? (o.kb >> 5) : 0u)];
+            const bool cand = vote && ((nb >> (o.kb & 31)) & 1u);
+            queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | o.kb, (unsigned)h), lane);
+            und |= (o.flo != o.fhi) & (!TAIL || valid);
         }
-        if (__any_sync(0xffffffffu, anyp)) {
+        if (__any_sync(0xffffffffu, und)) {
 #pragma unroll
             for (int r = 0; r < SPHI; ++r) {
                 const int c = j * SPHI + r;
-                unsigned kb;
-                bool vote, pend;
-                stage1(q_[r], dt, Rj, hf.G, hf.dmin, S2, H, T0, wlo, whi, nku, kb, vote, pend);
+                const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
                 int kk = -1;
-                if (pend && (!TAIL || valid)) kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                if ((o.flo != o.fhi) && (!TAIL || valid) && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi))
+                    kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
                 const bool cand = kk >= 0 && ((S.nearb[c * nkw + (kk >> 5)] >> (kk & 31)) & 1u);
                 queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | (unsigned)kk, (unsigned)h),
                            lane);
@@ -677,7 +688,10 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, cons
         S.lpre = reinterpret_cast<int32_t*>(ptr);
         ptr += 4 * tcols * nkw;
         S.sortbuf = reinterpret_cast<int32_t*>(ptr);
+        ptr += 4 * nw * kSortCap;
+        S.active = reinterpret_cast<int32_t*>(ptr);
     }
+    __shared__ int s_nactive;
     uint2* q = S.queue + warp * kQueue;
     __shared__ int64_t sh[33];
     const int tiles_phi = (p.K.nphi + SPHI - 1) / SPHI;
@@ -717,6 +731,21 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, cons
         }
         if (!__syncthreads_or(any)) continue;
         for (int j = tid; j < nj; j += nthr) S.dt[j] = p.dtab[j0 + j];
+        // compacted list of the d0 columns that hold a peak in any of the tile's rows
+        if (warp == 0) {
+            int na = 0;
+            for (int jb = 0; jb < nj; jb += 32) {
+                const int j = jb + lane;
+                bool act = false;
+                if (j < nj)
+                    for (int r = 0; r < SPHI; ++r)
+                        for (int w = 0; w < nkw; ++w) act |= S.mask[(j * SPHI + r) * nkw + w] != 0u;
+                const unsigned b = __ballot_sync(0xffffffffu, act);
+                if (act) S.active[na + __popc(b & lanemask_lt())] = j;
+                na += __popc(b);
+            }
+            if (lane == 0) s_nactive = na;
+        }
         // near bits (a peak within `window`) and each peak's first CSR position
         for (int v = tid; v < tcols * nkw; v += nthr) {
             const int c = v / nkw, w = v - (v / nkw) * nkw;
@@ -748,13 +777,14 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, cons
         const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
         int qn = 0;
         __syncthreads();
+        const int na = s_nactive;
         const int64_t nfull = ((he - hb) / nthr) * nthr;
         for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
-            assoc_one_hit<SPHI, NK, false>(p, S, q, qn, cp, sp, nj, nk, nkw, h, true, lane);
+            assoc_one_hit<SPHI, NK, false>(p, S, q, qn, cp, sp, na, nk, nkw, h, true, lane);
         {
             const int64_t h = hb + nfull + tid;
             if (hb + nfull + (tid - lane) < he)
-                assoc_one_hit<SPHI, NK, true>(p, S, q, qn, cp, sp, nj, nk, nkw, h, h < he, lane);
+                assoc_one_hit<SPHI, NK, true>(p, S, q, qn, cp, sp, na, nk, nkw, h, h < he, lane);
         }
         queue_drain(p, S, q, qn, nkw, nk, lane);
         __syncthreads();
@@ -918,7 +948,7 @@ cudaError_t launch_detect(const PeakParams& p, cudaStream_t s) {
     detect_tile(p.nphi, p.nd, p.nk, &R, &TD);
     const int64_t items = (int64_t)p.n_events * ((p.nphi + R - 1) / R) * ((p.nd + TD - 1) / TD);
     const int grid = (int)std::min<int64_t>(items, 152 * 8);
-    detect_kernel<<<grid, 256, detect_smem(p.nphi, p.nd, p.nk), s>>>(p, R, TD);
+    detect_kernel<<<grid, 512, detect_smem(p.nphi, p.nd, p.nk), s>>>(p, R, TD);
     return cudaGetLastError();
 }
 

@@ -55,18 +55,19 @@ def stage1(x, y, c, s, d, K, rcp_err=0.0):
         r2 = fma(x, x, yy)
         r = np.sqrt(r2)
         R1 = r + K["dabs"]
-        P1 = fma(F(3.02), r, F(1.01) * K["dabs"])
+        P1 = fma(F(4.02), r, F(2.02) * K["dabs"])
         R1s = R1 * R1
         dmin = np.maximum(K["cD1"] * R1s, K["cD2"] * P1)
         # G >= 0.55 dmin: a cell with den <= dmin gets tau > 1/2 and is never certified
         G = np.maximum(fma(K["cG1"], R1s, K["cG2"] * P1), F(0.55) * dmin)
         q = fma(y, c, -(x * s))
+        qs = q * K["S2"]                                   # per (hit, row)
+        ds = (d.astype(np.float64) * np.float64(K["S2"])).astype(F)  # table: d * S2 rounded once
         Rj = r2 + d * d
-        a = q - d
+        a = qs - ds
         den = fma(-(d + d), q, Rj)
         rc = (1.0 / den.astype(np.float64) * (1.0 + rcp_err)).astype(F)
-        t = a * rc
-        w = fma(t, K["S2"], K["H"])
+        w = fma(a, rc, K["H"])
         tau = fma(G, np.abs(rc), K["T0"])
         lo, hi = w - tau, w + tau
         flo, fhi = np.floor(lo), np.floor(hi)
