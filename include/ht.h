@@ -205,6 +205,30 @@ int ht_phase_times(ht_ctx *ctx, float *ms);
  * out[2] cells decided in binary64.  reset != 0 zeroes them after reading. */
 int ht_filter_stats(ht_ctx *ctx, int64_t *out, int32_t reset);
 
+/* Peak finding that allocates nothing (no paper counterpart: a service for
+ * callers that cannot call cudaMalloc where they need peaks — code inside a
+ * framework that owns every device allocation, a real-time path that must
+ * not block on an allocation, code without a context to keep buffers in).
+ * Same rule and output order as ht_peaks, for n_events accumulators the
+ * caller already holds on the device: acc is uint32
+ * [n_events][n_phi][n_d0][n_kappa] (device), peaks[cap] and *count (true
+ * number of peaks, int64) are device outputs; asynchronous on `stream`.
+ * Scratch (per-column peak counts and bitmasks, scan partials) lives in one
+ * fixed device array of HT_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until exit; a call needs
+ * n_events * n_phi * n_d0 * (12 + 6 * ceil(n_kappa / 32)) bytes plus ~5 KB of
+ * it (256 x 32 x 128 grid: about 113 events per call) and returns
+ * HT_ERR_BUDGET when that does not fit (nothing runs).  The array is looked
+ * up on the first call on each device (make that first call before any
+ * stream capture); every call on a device shares it and starts by clearing
+ * what must be zero, so calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Calls no
+ * cudaMalloc/cudaFree.  HT_ERR_INVALID_ARG for a bad grid or pointer,
+ * HT_ERR_CUDA if a launch fails. */
+#define HT_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ht_peaks_noalloc(const ht_grid *grid, const uint32_t *acc, int32_t n_events, uint32_t threshold,
+                     ht_peak *peaks, int64_t cap, int64_t *count, void *stream);
+
 /* Diagnostic (no paper counterpart): accuracy of the float32 reciprocal
  * approximation the stage-1 bound relies on, over `count` consecutive float
  * bit patterns starting at first_bits (positive normal floats).

@@ -45,7 +45,7 @@ HT_MODE_PLAIN = 1
 
 EXPORTS = ("ht_create", "ht_destroy", "ht_set_option", "ht_get_option", "ht_vote", "ht_peaks",
            "ht_associate", "ht_process", "ht_get_accumulator", "ht_get_tables", "ht_sync",
-           "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_check_rcp", "ht_strerror", "ht_last_error")
+           "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_peaks_noalloc", "ht_check_rcp", "ht_strerror", "ht_last_error")
 
 PEAK_DTYPE = np.dtype([("event", np.int32), ("i_phi", np.int32), ("i_d0", np.int32),
                        ("i_kappa", np.int32), ("votes", np.uint32)])
@@ -107,6 +107,7 @@ def load() -> ctypes.CDLL:
         "ht_filter_stats": [P, P, i32],
         "ht_phase_times": [P, P],
         "ht_check_rcp": [u32, u32, P],
+        "ht_peaks_noalloc": [P, P, i32, u32, P, i64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -335,6 +336,15 @@ def ht_phase_times(ctx):
     ms = np.zeros(3, np.float32)
     _check(load().ht_phase_times(ctx, ms.ctypes.data), ctx)
     return float(ms[0]), float(ms[1]), float(ms[2])
+
+
+def ht_peaks_noalloc(grid, acc, n_events, threshold, peaks, cap, count, stream=None):
+    """Peaks of device accumulators with no device allocation (see ht.h).
+    acc, peaks (int32 [cap, 5]) and count (int64 [1]) are CUDA tensors."""
+    g = HtGrid(int(grid.n_phi), int(grid.n_d0), int(grid.n_kappa), float(grid.d0_min), float(grid.d0_max),
+               float(grid.kappa_min), float(grid.kappa_max))
+    return _check(load().ht_peaks_noalloc(ctypes.byref(g), _ptr(acc), int(n_events), int(threshold), _ptr(peaks),
+                                          int(cap), _ptr(count), _stream_ptr(stream)))
 
 
 def ht_check_rcp(first_bits, count):
