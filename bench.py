@@ -181,7 +181,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[args.workload]
     g = w.grid
     batch = synth.generate(w, n_events=args.events, seed=w.seed + 1000 * rank if rank else None)
     n_events, n_hits = batch.n_events, batch.n_hits
@@ -190,13 +190,20 @@ def run_gpu(args):
 
     ctx = ht.Context(g, w.spec.layers)
     ctx.set_option(ht.HT_OPT_PHASE_TIMING, 1)
+    if args.waves_of:
+        # accumulator memory admitted for this many events at a time (waves)
+        ctx.set_option(ht.HT_OPT_ACC_BUDGET, args.waves_of * 4 * g.n_phi * g.n_d0 * g.n_kappa)
     hits_d = ht.Hits.from_batch(batch, device=dev)
+    if args.prune:
+        ctx.set_option(ht.HT_OPT_PRUNE, args.prune)
     if args.tile:
         for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
             ctx.set_option(k, int(v))
     else:
-        # autotune the vote tile on a 256-event sample (outside the timed region)
-        sample = batch.select(range(0, n_events, max(1, n_events // 256)))
+        # autotune the vote tile on a sample of the batch (outside the timed region)
+        per_ev = 4 * g.n_phi * g.n_d0 * g.n_kappa
+        n_s = max(1, min(256, n_events, ctx.get_option(ht.HT_OPT_ACC_BUDGET) // per_ev))
+        sample = batch.select(range(0, n_events, max(1, n_events // n_s))[:n_s])
         ctx.autotune(ht.Hits.from_batch(sample, device=dev))
     tile = {"tile_phi": ctx.get_option(ht.HT_OPT_TILE_PHI), "tile_d0": ctx.get_option(ht.HT_OPT_TILE_D0),
             "threads": ctx.get_option(ht.HT_OPT_THREADS)}
@@ -252,6 +259,8 @@ def run_gpu(args):
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_events / (ms / 1e3), "ms_per_step": ms,
+                              "workload": args.workload, "hit_votes_per_s": world * hit_votes / (ms / 1e3),
+                              "prune": ctx.get_option(ht.HT_OPT_PRUNE),
                               "events": n_events, "phase_ms": {"vote": float(np.mean(vote_ms)),
                                                                "peaks_assoc": float(np.mean(rest_ms))},
                               "peaks": int(counts[0]), "pairs": int(counts[1]), "tile": tile}), flush=True)
@@ -329,6 +338,10 @@ def run_gpu(args):
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     vote_s = float(np.mean(vote_ms)) / 1e3
     ops_per_cell = 6  # add, fma, reciprocal, multiply, fma, bin test: the formula's minimum per cell
+    # DRAM read + write of the vote kernel from ncu on the 512-event case of this
+    # workload (profiles/vote_kernel_batch512.md: 0.0186 + 2.0867 GB), scaled to a
+    # full launch by the events processed (the traffic is the accumulator write)
+    vote_traffic = (0.018555 + 2.086702) * 1e9 * n_events / 512
     cells_per_launch = hit_votes
     achieved = ops_per_cell * cells_per_launch / vote_s / 1e12
     peak_tops = sms * 128 * sm_mhz * 1e6 / 1e12
@@ -347,7 +360,7 @@ def run_gpu(args):
         "batched_over_plain": (n_events / (ms / 1e3)) / plain_eps,
         "phase_ms": {"vote": float(np.mean(vote_ms)), "peaks_assoc": float(np.mean(rest_ms))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops, "traffic": None,
+                     "frac": achieved / peak_tops, "traffic": vote_traffic,
                      "kernel": "vote_kernel", "ops_per_cell": ops_per_cell,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"},
         "hbm": {"step_bytes_min": 2 * acc_bytes + 8.0 * n_hits,
@@ -376,6 +389,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--prune", type=int, default=0, help="HT_OPT_PRUNE bits (1 vote, 2 association)")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload name (secondary lines use --no-extras)")
+    ap.add_argument("--waves-of", type=int, default=0, help="admit accumulators for this many events at a time")
     ap.add_argument("--events", type=int, default=None, help="events per batch (default: the full 4096)")
     ap.add_argument("--tile", default="", help="vote tile 'phi,d0,threads' instead of autotuning")
     ap.add_argument("--no-extras", action="store_true",

@@ -127,6 +127,9 @@ typedef struct {
 #define HT_OPT_LAUNCHES 9          /* read-only: kernels launched by the last ht_process */
 #define HT_OPT_ATILE_PHI 10        /* phi0 rows per association tile: 1, 2, 4 or 8 (0 = auto) */
 #define HT_OPT_ATILE_D0 11         /* d0 columns per association tile (0 = auto) */
+#define HT_OPT_PRUNE 12            /* bit 0: the vote, bit 1: the association walk only each (hit,
+                                      phi0) row's d0 band that can hold a vote (a proven superset)
+                                      instead of every cell; same results.  Default 0. */
 
 #define HT_MODE_BATCHED 0 /* one persistent launch per kernel over all (event, tile) items */
 #define HT_MODE_PLAIN 1   /* one launch sequence per event */

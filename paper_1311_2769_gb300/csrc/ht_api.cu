@@ -75,12 +75,14 @@ struct ht_ctx {
     int mode = HT_MODE_BATCHED;
     int tile_phi = 0, tile_d = 0, threads = 0;
     int atile_phi = 0, atile_d = 0;  // association tile (0 = auto)
+    int prune = 0;                   // bit 0: vote, bit 1: association walk only d0 bands
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
 
     // resolved tile configuration
     int r_tile_phi = 1, r_tile_d = 1, r_threads = 256, r_smem = 0, r_blocks_per_sm = 1;
+    bool r_band = false, a_band = false;
     int a_tile_phi = 1, a_tile_d = 1, a_threads = 256, a_smem = 0;  // association tile
 
     int gen = 0;  // buffer generation (graph invalidation)
@@ -216,6 +218,18 @@ KConsts make_consts(const ht_grid& g, const std::vector<float>& d0) {
     K.cGb1 = (float)(64.0 * u * u * V2);
     K.cGb2 = (float)(20.0 * u * u * S2);
     K.cDb = (float)std::ldexp(1.0, -23);
+    // d0 bands (pruned vote): kappa window widened by two bins
+    {
+        const double kmn = (double)g.kappa_min, kmx = (double)g.kappa_max, dk = (kmx - kmn) / nk;
+        const double A = kmn - 2.0 * dk, B = kmx + 2.0 * dk;
+        K.band_ok = (A < 0.0 && B > 0.0) ? 1 : 0;
+        K.bA2 = (float)(A * A);
+        K.bB2 = (float)(B * B);
+        K.biA = (float)(1.0 / std::fabs(A));
+        K.biB = (float)(1.0 / B);
+        K.bdfirst = d0.empty() ? 0.0f : d0[0];
+        K.bidd = (float)((double)g.n_d0 / ((double)g.d0_max - (double)g.d0_min));
+    }
     return K;
 }
 
@@ -246,12 +260,15 @@ int resolve_tiles(ht_ctx* ctx) {
             }
     }
     int thr = ctx->threads > 0 ? ctx->threads : 256;
-    const int smem = vote_smem_bytes(tp, td, nk);
+    const bool band = (ctx->prune & 1) && ctx->K.band_ok;
+    ctx->a_band = (ctx->prune & 2) && ctx->K.band_ok;
+    const int smem = vote_smem_bytes(tp, td, nk, thr, band);
     if (smem > 227 * 1024)
         return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d needs %d B of shared memory", tp, td, nk, smem);
-    CU(vote_prepare(tp, nk, smem));
+    CU(vote_prepare(tp, nk, smem, band));
     int per_sm = 0;
-    CU(vote_occupancy(tp, nk, thr, smem, &per_sm));
+    CU(vote_occupancy(tp, nk, thr, smem, &per_sm, band));
+    ctx->r_band = band;
     if (per_sm < 1) return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d with %d threads cannot launch", tp, td, nk, thr);
     ctx->r_tile_phi = tp;
     ctx->r_tile_d = td;
@@ -264,10 +281,11 @@ int resolve_tiles(ht_ctx* ctx) {
     const int atp = ctx->atile_phi > 0 ? std::min(ctx->atile_phi, 8) : std::min(4, ctx->grid.n_phi >= 4 ? 4 : 1);
     int atd = ctx->atile_d > 0 ? std::min(ctx->atile_d, nd) : std::min(nd, 16);
     const int athr = std::min(thr, 256);
-    while (atd > 1 && assoc_smem(atp, atd, nk, athr) > 200 * 1024) atd = (atd + 1) / 2;
-    const int asmem = (int)assoc_smem(atp, atd, nk, athr);
+    const bool aband = ctx->a_band;
+    while (atd > 1 && assoc_smem(atp, atd, nk, athr, aband) > 200 * 1024) atd = (atd + 1) / 2;
+    const int asmem = (int)assoc_smem(atp, atd, nk, athr, aband);
     if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association tile does not fit shared memory");
-    CU(assoc_prepare(atp, nk, asmem));
+    CU(assoc_prepare(atp, nk, asmem, aband));
     ctx->a_tile_phi = atp;
     ctx->a_tile_d = atd;
     ctx->a_threads = athr;
@@ -375,9 +393,9 @@ int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStrea
         CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
         CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), s));
         const int grid = std::min<int64_t>(p.n_items, (int64_t)ctx->sms * ctx->r_blocks_per_sm);
-        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s));
+        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s, ctx->r_band));
     } else {
-        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s));
+        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_band));
     }
     return HT_OK;
 }
@@ -454,6 +472,7 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, i
     a.hit_idx = hit_idx;
     a.pair_cap = pair_cap;
     a.window = window;
+    a.band = ctx->a_band ? 1 : 0;
     a.cphi = ctx->d_cphi;
     a.sphi = ctx->d_sphi;
     a.dtab = ctx->d_dtab;
@@ -675,6 +694,10 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             break;
         case HT_OPT_COUNT_STAGES: ctx->count_stages = value != 0; break;
         case HT_OPT_USE_GRAPH: ctx->use_graph = value != 0; break;
+        case HT_OPT_PRUNE:
+            if (value < 0 || value > 3) return fail(ctx, HT_ERR_INVALID_ARG, "prune must be 0..3");
+            ctx->prune = (int)value;
+            break;
         case HT_OPT_ATILE_PHI:
             if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
                 return fail(ctx, HT_ERR_INVALID_ARG, "association tile_phi must be 0, 1, 2, 4 or 8");
@@ -693,7 +716,7 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
     }
     ctx->gvalid = false;
     if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS || key == HT_OPT_ATILE_PHI ||
-        key == HT_OPT_ATILE_D0) {
+        key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE) {
         int st = resolve_tiles(ctx);
         if (st) return st;
     }
@@ -712,6 +735,7 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_USE_GRAPH: *value = ctx->use_graph; break;
         case HT_OPT_PHASE_TIMING: *value = ctx->timing; break;
         case HT_OPT_ATILE_PHI: *value = ctx->a_tile_phi; break;
+        case HT_OPT_PRUNE: *value = (ctx->r_band ? 1 : 0) | (ctx->a_band ? 2 : 0); break;
         case HT_OPT_ATILE_D0: *value = ctx->a_tile_d; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
@@ -737,7 +761,7 @@ int ht_vote(ht_ctx* ctx, const ht_hits* hits, void* stream) {
         for (int32_t e = 0; e < ctx->c_events; ++e) {
             VoteParams p = vote_params(ctx, e, 1, false);
             p.acc = ctx->acc.p + (int64_t)e * ctx->cells;
-            CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s));
+            CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_band));
         }
     } else {
         st = run_vote(ctx, 0, ctx->c_events, true, s);
@@ -822,6 +846,7 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     a.hit_idx = ctx->hitidx.p;
     a.pair_cap = total;
     a.window = window;
+    a.band = ctx->a_band ? 1 : 0;
     a.cphi = ctx->d_cphi;
     a.sphi = ctx->d_sphi;
     a.dtab = ctx->d_dtab;
@@ -1024,7 +1049,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     for (int tp : {1, 2, 4, 8}) {
         if (tp > ctx->grid.n_phi) continue;
         for (int td : tds) {
-            const int smem = vote_smem_bytes(tp, td, nk);
+            const int smem = vote_smem_bytes(tp, td, nk, 256, (ctx->prune & 1) && ctx->K.band_ok);
             if (smem > 200 * 1024 || smem < 8 * 1024) continue;
             for (int thr : {128, 256}) {
                 ctx->tile_phi = tp;

@@ -62,6 +62,7 @@ struct AssocParams {
     int32_t* hit_idx;
     int64_t pair_cap;
     int32_t window;
+    int32_t band;           // 1: walk each (hit, row)'s d0 band only
     const float* cphi;
     const float* sphi;
     const float4* dtab;
@@ -86,11 +87,12 @@ struct ScanRange {
 constexpr int kScanBlocks = 304;
 constexpr int kScanThreads = 1024;
 
-int vote_smem_bytes(int tile_phi, int tile_d, int nk);
-cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes);
-cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks);
+int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band);
+cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes, bool band);
+cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, bool band);
 cudaError_t launch_finalize(int64_t* scal, cudaStream_t s);
-cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s);
+cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s,
+                        bool band);
 cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer, int64_t n_hits,
                             const int32_t* offs, int32_t n_events, int32_t n_layers, int32_t* err,
                             cudaStream_t s);
@@ -103,8 +105,8 @@ cudaError_t launch_emit(const PeakParams& p, cudaStream_t s);
 cudaError_t launch_paircount(const PeakParams& p, const int64_t* lo_dev, const int64_t* hi_dev,
                              cudaStream_t s);
 cudaError_t launch_scan(const ScanRange& r, int64_t* scratch /* 2 * kScanBlocks */, cudaStream_t s);
-size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads);
-cudaError_t assoc_prepare(int tile_phi, int nk, int smem);
+size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads, bool band);
+cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band);
 cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int tile_d, int threads, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
 

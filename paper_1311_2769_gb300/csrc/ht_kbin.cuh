@@ -45,7 +45,46 @@ struct KConsts {
     float cDb;                  // den_min2 = cDb * R1^2
     // stage 3 (binary64 definition)
     double kmin, scale;
+    // d0 band of a (hit, phi row): kappa window widened by two bins each side
+    int band_ok;           // 0: kappa range does not straddle 0, bands are the full tile
+    float bA2, bB2, biA, biB, bdfirst, bidd;
 };
+
+// The d0 columns [jlo, jhi] of the tile [j0, j0 + nj) where hit (x, y) can vote
+// in the row with table values (c, s), as a superset: with u = d0 - q and
+// p^2 = r^2 - q^2 the curvature is -2u / (u^2 + p^2); it lies in [A, B)
+// (A < 0 < B, the kappa range widened by two bins) outside the forbidden
+// intervals (a1, a2) (kappa < A) and [b1, b2] (kappa >= B), whose ends are
+// roots of A u^2 + 2u + A p^2 = 0 and B u^2 + 2u + B p^2 = 0.  The hull of
+// the allowed u in the tile is widened by one column below and two above.
+// Returns jhi < jlo when the tile holds no allowed column.
+__device__ __forceinline__ void d0_band(float r2, float q, float dlo, float dhi, int j0, int nj, const KConsts& K,
+                                        int& jlo, int& jhi) {
+    const float BIG = 1e30f;
+    const float p2 = fmaxf(fmaf(-q, q, r2), 0.0f);
+    const float DA = fmaf(-K.bA2, p2, 1.0f);
+    const float DB = fmaf(-K.bB2, p2, 1.0f);
+    const float sA = sqrtf(fmaxf(DA, 0.0f));
+    const float sB = sqrtf(fmaxf(DB, 0.0f));
+    const float a1 = DA > 0.0f ? ((K.bA2 * p2) * K.biA) / (1.0f + sA) : BIG;
+    const float a2 = DA > 0.0f ? (1.0f + sA) * K.biA : BIG;
+    const float b2 = DB > 0.0f ? ((-(K.bB2 * p2)) * K.biB) / (1.0f + sB) : -BIG;
+    const float b1 = DB > 0.0f ? (-(1.0f + sB)) * K.biB : -BIG;
+    const float ulo = dlo - q, uhi = dhi - q;
+    const float lo = ulo < b1 ? ulo
+                              : ((ulo <= a1) & (uhi > b2) ? fmaxf(ulo, b2) : (uhi >= a2 ? fmaxf(ulo, a2) : BIG));
+    const float hi = uhi >= a2 ? uhi
+                               : ((uhi > b2) & (ulo <= a1) ? fminf(uhi, a1) : (ulo < b1 ? fminf(uhi, b1) : -BIG));
+    if (!(lo <= hi)) {
+        jlo = j0 + nj;
+        jhi = j0 - 1;
+        return;
+    }
+    const float jl = floorf(((lo + q) - K.bdfirst) * K.bidd) - 1.0f;
+    const float jh = floorf(((hi + q) - K.bdfirst) * K.bidd) + 2.0f;
+    jlo = (int)fminf(fmaxf(jl, (float)j0), (float)(j0 + nj));
+    jhi = (int)fminf(fmaxf(jh, (float)(j0 - 1)), (float)(j0 + nj - 1));
+}
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;

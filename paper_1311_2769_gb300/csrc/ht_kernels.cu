@@ -193,6 +193,196 @@ __global__ void __launch_bounds__(256, 3) vote_kernel(const VoteParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// pruned vote: only the d0 band of each (hit, phi row) is evaluated
+// ---------------------------------------------------------------------------
+// Per chunk of blockDim hits: every thread computes its hit's band over the
+// tile's rows (the union of the rows' d0_band) and files the hit into one of
+// four buckets by band length (<= nj/8, nj/4, nj/2, nj).  Warps then take 32
+// hits of one bucket at a time; each lane walks its own band from its own
+// first column, the warp for as many steps as the longest band among its 32
+// lanes, so lanes of a warp do similar amounts of work.  Cells outside every
+// band cannot vote (they are out of the kappa range in binary64), so the
+// accumulator is the same as the full vote's.
+constexpr int kBuckets = 4;
+
+template <int SPHI, int NK>
+__global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* dt_s = reinterpret_cast<float4*>(smem_raw);
+    const int nthr = blockDim.x;
+    // chunk records follow the d0 table; the accumulator tile follows them
+    float* sx = reinterpret_cast<float*>(smem_raw + 16 * p.tile_d);
+    float* sy = sx + nthr;
+    int* sband = reinterpret_cast<int*>(sy + nthr);           // jlo | (len << 16)
+    uint16_t* slist = reinterpret_cast<uint16_t*>(sband + nthr);  // [kBuckets][nthr]
+    uint32_t* acc_s = reinterpret_cast<uint32_t*>(slist + kBuckets * nthr + (nthr & 1 ? 2 : 0));
+    __shared__ int s_item;
+    __shared__ int s_cnt[kBuckets];
+
+    const int nk = NK ? NK : p.K.nk;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    const int tiles = p.tiles_phi * p.tiles_d;
+    const int col_words = SPHI * nk;
+    const uint32_t acc_sh = smem_addr(acc_s);
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    const unsigned nku = (unsigned)nk;
+
+    for (int it = 0;; ++it) {
+        int item;
+        if (p.queue) {
+            if (tid == 0) s_item = atomicAdd(p.queue, 1);
+            __syncthreads();
+            item = s_item;
+        } else {
+            if (it > 0) break;
+            item = p.item0 + blockIdx.x;
+        }
+        if (item >= p.n_items) break;
+        const int el = item / tiles;
+        const int t = item - el * tiles;
+        const int e = p.order ? p.order[el] : el;
+        const int tp = t / p.tiles_d;
+        const int td = t - tp * p.tiles_d;
+        const int i0 = tp * SPHI;
+        const int j0 = td * p.tile_d;
+        const int nj = min(p.tile_d, p.K.nd - j0);
+        const int nrows = min(SPHI, p.K.nphi - i0);
+        const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
+        const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
+
+        for (int w = tid; w < nj * col_words; w += nthr) acc_s[w] = 0u;
+        for (int j = tid; j < nj; j += nthr) dt_s[j] = p.dtab[j0 + j];
+        float cp[SPHI], sp[SPHI];
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            const int i = r < nrows ? i0 + r : i0;
+            cp[r] = p.cphi[i];
+            sp[r] = p.sphi[i];
+        }
+        const float dlo = p.dtab[j0].x, dhi = p.dtab[j0 + nj - 1].x;
+        int lim[kBuckets];
+        lim[0] = max(1, nj / 8);
+        lim[1] = max(1, nj / 4);
+        lim[2] = max(1, nj / 2);
+        lim[3] = nj;
+        if (p.stats && tid == 0) atomicAdd(&p.stats[0], (unsigned long long)((he - hb) * nrows * nj));
+
+        for (int64_t cb = hb; cb < he; cb += nthr) {
+            if (tid < kBuckets) s_cnt[tid] = 0;
+            __syncthreads();
+            // phase 1: band of this thread's hit over the tile's rows, filed by length
+            const int64_t h = cb + tid;
+            int jlo = j0 + nj, jhi = j0 - 1;
+            float x = 0.0f, y = 0.0f;
+            if (h < he) {
+                x = p.x[h];
+                y = p.y[h];
+                if (p.K.band_ok) {
+                    const float r2 = fmaf(x, x, __fmul_rn(y, y));
+#pragma unroll
+                    for (int r = 0; r < SPHI; ++r) {
+                        if (r >= nrows) break;
+                        int a, b;
+                        d0_band(r2, q_of(x, y, cp[r], sp[r]), dlo, dhi, j0, nj, p.K, a, b);
+                        if (b >= a) {
+                            jlo = min(jlo, a);
+                            jhi = max(jhi, b);
+                        }
+                    }
+                } else {
+                    jlo = j0;
+                    jhi = j0 + nj - 1;
+                }
+            }
+            const int len = jhi >= jlo ? jhi - jlo + 1 : 0;
+            sx[tid] = x;
+            sy[tid] = y;
+            sband[tid] = (jlo - j0) | (len << 16);
+#pragma unroll
+            for (int bk = 0; bk < kBuckets; ++bk) {
+                const bool in = len > 0 && len <= lim[bk] && (bk == 0 || len > lim[bk - 1]);
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                int base = 0;
+                if (lane == 0 && m) base = atomicAdd(&s_cnt[bk], __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (in) slist[bk * nthr + base + __popc(m & lanemask_lt())] = (uint16_t)tid;
+            }
+            __syncthreads();
+            // phase 2: warps take 32 hits of one bucket at a time
+            int groups = 0;
+            int gstart[kBuckets + 1];
+#pragma unroll
+            for (int bk = 0; bk < kBuckets; ++bk) {
+                gstart[bk] = groups;
+                groups += (s_cnt[bk] + 31) >> 5;
+            }
+            gstart[kBuckets] = groups;
+            for (int g = warp; g < groups; g += nw) {
+                int bk = 0;
+#pragma unroll
+                for (int b2 = 1; b2 < kBuckets; ++b2) bk += g >= gstart[b2];
+                const int idx = (g - gstart[bk]) * 32 + lane;
+                const bool has = idx < s_cnt[bk];
+                const int ht = has ? slist[bk * nthr + idx] : 0;
+                const int bd = has ? sband[ht] : 0;
+                const int jl = bd & 0xFFFF, ln = bd >> 16;
+                const float hx = sx[ht], hy = sy[ht];
+                const HitFast hf = hit_fast(hx, hy, p.K);
+                float q[SPHI], qs[SPHI];
+#pragma unroll
+                for (int r = 0; r < SPHI; ++r) {
+                    q[r] = q_of(hx, hy, cp[r], sp[r]);
+                    qs[r] = q[r] * S2;
+                }
+                const int steps = __reduce_max_sync(0xffffffffu, ln);
+                for (int s = 0; s < steps; ++s) {
+                    const bool live = s < ln;
+                    const int j = live ? jl + s : 0;
+                    const float4 dt = dt_s[j];
+                    const float Rj = hf.r2 + dt.z;
+                    const uint32_t col_sh = acc_sh + 4u * (unsigned)(j * col_words);
+                    bool und = false;
+#pragma unroll
+                    for (int r = 0; r < SPHI; ++r) {
+                        const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+                        red_if_vote(col_sh + 4u * ((unsigned)(r * nk) + o.kb), o.flo, o.fhi, o.kb, nku, live);
+                        und |= (o.flo != o.fhi) & live;
+                    }
+                    if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+                        for (int r = 0; r < SPHI; ++r) {
+                            const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+                            if ((o.flo != o.fhi) && live && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi)) {
+                                const int kk = cell_slow(hx, hy, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                                if (kk >= 0) atomicAdd(acc_s + j * col_words + r * nk + kk, 1u);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
+        const int nrj = nrows * nj;
+        for (int row = warp; row < nrj; row += nw) {
+            const int r = row / nj;
+            const int j = row - r * nj;
+            const uint32_t* src = acc_s + j * col_words + r * nk;
+            uint32_t* dst = dst_e + ((int64_t)(i0 + r) * p.K.nd + (j0 + j)) * nk;
+            if ((nk & 3) == 0) {
+                const uint4* s4 = reinterpret_cast<const uint4*>(src);
+                uint4* d4 = reinterpret_cast<uint4*>(dst);
+                for (int kk = lane; kk < (nk >> 2); kk += 32) d4[kk] = s4[kk];
+            } else {
+                for (int kk = lane; kk < nk; kk += 32) dst[kk] = src[kk];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // input validation (device-resident batches)
 // bit 1: non-finite or |coordinate| > 1e4; bit 2: layer out of range; bit 4: offsets
 // ---------------------------------------------------------------------------
@@ -295,42 +485,53 @@ __global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const i
             }
         }
         __syncthreads();
-        // interior columns: warp per (row, column), lanes over kappa
+        // interior columns: warp per (row, column), lanes over kappa.  Every lane
+        // reads its 3x3x3 box (absent neighbours read as -1 in int32, so they
+        // never reject) and compares against the maximum of the neighbours that
+        // precede it in linear order (strictly) and of those that follow it.
         for (int cc = warp; cc < nr * nj; cc += nw) {
             const int r = cc / nj, j = cc - (cc / nj) * nj;
             const int i = i0 + r;
-            // actual neighbour rows and whether they precede row i in linear order
-            const int im = i == 0 ? p.nphi - 1 : i - 1, ip = i == p.nphi - 1 ? 0 : i + 1;
             const int64_t col = ((int64_t)e * p.nphi + i) * p.nd + (j0 + j);
-            const uint32_t* ctr = tile + ((int64_t)(r + 1) * tcols + (j + 1)) * nk;
+            // row di = -1 / +1 precedes row i unless the phi wrap makes it follow
+            // (one row only: those rows are the row itself, covered by di = 0)
+            const bool single = p.nphi == 1;
+            const bool m_earlier = i > 0, p_earlier = i == p.nphi - 1;
             int count = 0;
             for (int k0 = 0, w = 0; k0 < nk; k0 += 32, ++w) {
                 const int kk = k0 + lane;
                 bool pk = false;
                 if (kk < nk) {
-                    const uint32_t v = ctr[kk];
-                    if (v >= p.thr) {
-                        pk = true;
-                        for (int di = -1; di <= 1 && pk; ++di) {
-                            const int ii = di < 0 ? im : (di > 0 ? ip : i);
-                            const uint32_t* rowp = tile + ((int64_t)(r + 1 + di) * tcols) * nk;
-                            for (int dj = -1; dj <= 1 && pk; ++dj) {
-                                const uint32_t* cp = rowp + (j + 1 + dj) * nk;
-                                for (int dk = -1; dk <= 1; ++dk) {
-                                    const int k2 = kk + dk;
-                                    if (k2 < 0 || k2 >= nk) continue;
-                                    if (ii == i && dj == 0 && dk == 0) continue;  // the cell itself
-                                    const uint32_t u = cp[k2];
-                                    if (u == kAbsent) continue;
-                                    const bool earlier = ii < i || (ii == i && (dj < 0 || (dj == 0 && dk < 0)));
-                                    if (earlier ? !(v > u) : !(v >= u)) {
-                                        pk = false;
-                                        break;
-                                    }
+                    const int v = (int)tile[((int64_t)(r + 1) * tcols + (j + 1)) * nk + kk];
+                    int mE = -1, mL = -1;
+#pragma unroll
+                    for (int di = -1; di <= 1; ++di) {
+                        if (single && di != 0) continue;
+                        const int* rowp = reinterpret_cast<const int*>(tile) + ((int64_t)(r + 1 + di) * tcols) * nk;
+#pragma unroll
+                        for (int dj = -1; dj <= 1; ++dj) {
+                            const int* cp2 = rowp + (j + 1 + dj) * nk;
+                            const int u0 = cp2[kk];
+                            const int um = kk > 0 ? cp2[kk - 1] : -1;
+                            const int up = kk + 1 < nk ? cp2[kk + 1] : -1;
+                            if (di == 0) {
+                                if (dj < 0) {
+                                    mE = max(mE, max(u0, max(um, up)));
+                                } else if (dj > 0) {
+                                    mL = max(mL, max(u0, max(um, up)));
+                                } else {
+                                    mE = max(mE, um);
+                                    mL = max(mL, up);
                                 }
+                            } else {
+                                const int m3 = max(u0, max(um, up));
+                                const bool earlier = di < 0 ? m_earlier : p_earlier;
+                                if (earlier) mE = max(mE, m3);
+                                else mL = max(mL, m3);
                             }
                         }
                     }
+                    pk = (uint32_t)v >= p.thr && v > mE && v >= mL;
                 }
                 const unsigned b = __ballot_sync(0xffffffffu, pk);
                 if (lane == 0) {
@@ -411,9 +612,13 @@ __global__ void paircount_kernel(const PeakParams p, const int64_t* lo_dev, cons
 // ---------------------------------------------------------------------------
 // scan (reduce, spine, down-sweep over contiguous per-block segments)
 // ---------------------------------------------------------------------------
+// [lo, hi) clamped to [0, cap]: both ends, so that out[hi] (write_end) stays
+// inside an output of cap + 1 entries even when a whole wave lies past the cap
 __device__ void scan_bounds(const ScanRange& r, int64_t& lo, int64_t& hi) {
     lo = r.lo_dev ? *r.lo_dev : r.lo;
     hi = r.hi_dev ? *r.hi_dev : r.hi;
+    if (lo > r.cap) lo = r.cap;
+    if (lo < 0) lo = 0;
     if (hi > r.cap) hi = r.cap;
     if (hi < lo) hi = lo;
 }
@@ -532,12 +737,18 @@ struct AssocSmem {
     uint2* queue;      // [warps][kQueue] (column << 16 | kappa bin, hit)
     int32_t* sortbuf;  // [warps][kSortCap]
     int32_t* active;   // [tile_d] d0 columns of the tile holding any peak
+    float* sx;         // [threads] band bucketing records of the current hit chunk
+    float* sy;
+    int* sband;
+    uint16_t* slist;   // [kBuckets][threads]
+    int* cnt;          // [kBuckets] bucket fill counts
 };
 
-__host__ __device__ inline size_t assoc_smem_bytes(int tile_phi, int tile_d, int nk, int threads) {
+__host__ __device__ inline size_t assoc_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band) {
     const size_t cols = (size_t)tile_phi * tile_d, nkw = (nk + 31) / 32;
     return 16 * (size_t)tile_d + cols * nkw * (4 + 4 + 4 + 8) + cols * ((nk + 1) / 2) * 8 +
-           (size_t)(threads / 32) * (kQueue * 8 + kSortCap * 4) + 4 * (size_t)tile_d + 64;
+           (size_t)(threads / 32) * (kQueue * 8 + kSortCap * 4) + 4 * (size_t)tile_d +
+           (band ? (size_t)threads * (4 + 4 + 4 + 2 * kBuckets) : 0) + 64;
 }
 
 // One queued candidate (column c of the tile, kappa bin kb, hit h): append h
@@ -629,6 +840,118 @@ __device__ __forceinline__ void assoc_one_hit(const AssocParams& p, const AssocS
     }
 }
 
+// Association over d0 bands: the vote's bucketing (see vote_band_kernel),
+// bands clipped to the tile's columns [ja, ja + nja) that hold peaks.
+template <int SPHI, int NK>
+__device__ __forceinline__ void assoc_band_hits(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn,
+                                                const float* cp, const float* sp, int ja, int nja, int j0,
+                                                int nrows, int nk, int nkw, int64_t hb, int64_t he, int lane) {
+    const int nthr = blockDim.x, tid = threadIdx.x, warp = tid >> 5, nw = nthr >> 5;
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    const unsigned nku = (unsigned)nk;
+    const float dlo = S.dt[ja - j0].x, dhi = S.dt[ja - j0 + nja - 1].x;
+    int lim[kBuckets];
+    lim[0] = max(1, nja / 8);
+    lim[1] = max(1, nja / 4);
+    lim[2] = max(1, nja / 2);
+    lim[3] = nja;
+    for (int64_t cb = hb; cb < he; cb += nthr) {
+        if (tid < kBuckets) S.cnt[tid] = 0;
+        __syncthreads();
+        const int64_t h = cb + tid;
+        int jlo = ja + nja, jhi = ja - 1;
+        float x = 0.0f, y = 0.0f;
+        if (h < he) {
+            x = p.x[h];
+            y = p.y[h];
+            const float r2 = fmaf(x, x, __fmul_rn(y, y));
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                if (r >= nrows) break;
+                int a, b;
+                d0_band(r2, q_of(x, y, cp[r], sp[r]), dlo, dhi, ja, nja, p.K, a, b);
+                if (b >= a) {
+                    jlo = min(jlo, a);
+                    jhi = max(jhi, b);
+                }
+            }
+        }
+        const int len = jhi >= jlo ? jhi - jlo + 1 : 0;
+        S.sx[tid] = x;
+        S.sy[tid] = y;
+        S.sband[tid] = (jlo - j0) | (len << 16);
+#pragma unroll
+        for (int bk = 0; bk < kBuckets; ++bk) {
+            const bool in = len > 0 && len <= lim[bk] && (bk == 0 || len > lim[bk - 1]);
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&S.cnt[bk], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (in) S.slist[bk * nthr + base + __popc(m & lanemask_lt())] = (uint16_t)tid;
+        }
+        __syncthreads();
+        int groups = 0;
+        int gstart[kBuckets + 1];
+#pragma unroll
+        for (int bk = 0; bk < kBuckets; ++bk) {
+            gstart[bk] = groups;
+            groups += (S.cnt[bk] + 31) >> 5;
+        }
+        gstart[kBuckets] = groups;
+        for (int g = warp; g < groups; g += nw) {
+            int bk = 0;
+#pragma unroll
+            for (int b2 = 1; b2 < kBuckets; ++b2) bk += g >= gstart[b2];
+            const int idx = (g - gstart[bk]) * 32 + lane;
+            const bool has = idx < S.cnt[bk];
+            const int ht = has ? S.slist[bk * nthr + idx] : 0;
+            const int bd = has ? S.sband[ht] : 0;
+            const int jl = bd & 0xFFFF, ln = bd >> 16;
+            const float hx = S.sx[ht], hy = S.sy[ht];
+            const int64_t hh = cb + ht;
+            const HitFast hf = hit_fast(hx, hy, p.K);
+            float q_[SPHI], qs[SPHI];
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                q_[r] = q_of(hx, hy, cp[r], sp[r]);
+                qs[r] = q_[r] * S2;
+            }
+            const int steps = __reduce_max_sync(0xffffffffu, ln);
+            for (int s = 0; s < steps; ++s) {
+                const bool live = s < ln;
+                const int j = live ? jl + s : ja - j0;
+                const float4 dt = S.dt[j];
+                const float Rj = hf.r2 + dt.z;
+                bool und = false;
+#pragma unroll
+                for (int r = 0; r < SPHI; ++r) {
+                    const int c = j * SPHI + r;
+                    const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+                    const bool vote = live & (o.flo == o.fhi) & (o.kb < nku);
+                    const uint32_t nb = S.nearb[c * nkw + (vote ? (o.kb >> 5) : 0u)];
+                    const bool cand = vote && ((nb >> (o.kb & 31)) & 1u);
+                    queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | o.kb, (unsigned)hh), lane);
+                    und |= (o.flo != o.fhi) & live;
+                }
+                if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+                    for (int r = 0; r < SPHI; ++r) {
+                        const int c = j * SPHI + r;
+                        const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+                        int kk = -1;
+                        if ((o.flo != o.fhi) && live && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi))
+                            kk = cell_slow(hx, hy, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                        const bool cand = kk >= 0 && ((S.nearb[c * nkw + (kk >> 5)] >> (kk & 31)) & 1u);
+                        queue_push(p, S, q, qn, nkw, nk, cand,
+                                   make_uint2(((unsigned)c << 16) | (unsigned)kk, (unsigned)hh), lane);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Ascending order of one CSR row (distinct hit indices) by rank sort.
 __device__ void sort_row(int32_t* seg, int n, int32_t* buf, int lane) {
     if (n <= 1) return;
@@ -663,7 +986,7 @@ __device__ void sort_row(int32_t* seg, int n, int32_t* buf, int lane) {
     __syncwarp();
 }
 
-template <int SPHI, int NK>
+template <int SPHI, int NK, bool BAND>
 __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, const int tile_d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = NK ? NK : p.K.nk;
@@ -690,7 +1013,20 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, cons
         S.sortbuf = reinterpret_cast<int32_t*>(ptr);
         ptr += 4 * nw * kSortCap;
         S.active = reinterpret_cast<int32_t*>(ptr);
+        ptr += 4 * tile_d;
+        if (BAND) {
+            S.sx = reinterpret_cast<float*>(ptr);
+            S.sy = S.sx + nthr;
+            S.sband = reinterpret_cast<int*>(S.sy + nthr);
+            S.slist = reinterpret_cast<uint16_t*>(S.sband + nthr);
+        } else {
+            S.sx = S.sy = nullptr;
+            S.sband = nullptr;
+            S.slist = nullptr;
+        }
     }
+    __shared__ int s_cnt[kBuckets];
+    S.cnt = s_cnt;
     __shared__ int s_nactive;
     uint2* q = S.queue + warp * kQueue;
     __shared__ int64_t sh[33];
@@ -778,13 +1114,19 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, cons
         int qn = 0;
         __syncthreads();
         const int na = s_nactive;
-        const int64_t nfull = ((he - hb) / nthr) * nthr;
-        for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
-            assoc_one_hit<SPHI, NK, false>(p, S, q, qn, cp, sp, na, nk, nkw, h, true, lane);
-        {
-            const int64_t h = hb + nfull + tid;
-            if (hb + nfull + (tid - lane) < he)
-                assoc_one_hit<SPHI, NK, true>(p, S, q, qn, cp, sp, na, nk, nkw, h, h < he, lane);
+        if (BAND && na > 0) {
+            // the active columns span [S.active[0], S.active[na-1]]: bands are clipped to it
+            const int ja = j0 + S.active[0], jb = j0 + S.active[na - 1];
+            assoc_band_hits<SPHI, NK>(p, S, q, qn, cp, sp, ja, jb - ja + 1, j0, nrows, nk, nkw, hb, he, lane);
+        } else {
+            const int64_t nfull = ((he - hb) / nthr) * nthr;
+            for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
+                assoc_one_hit<SPHI, NK, false>(p, S, q, qn, cp, sp, na, nk, nkw, h, true, lane);
+            {
+                const int64_t h = hb + nfull + tid;
+                if (hb + nfull + (tid - lane) < he)
+                    assoc_one_hit<SPHI, NK, true>(p, S, q, qn, cp, sp, na, nk, nkw, h, h < he, lane);
+            }
         }
         queue_drain(p, S, q, qn, nkw, nk, lane);
         __syncthreads();
@@ -837,8 +1179,9 @@ __global__ void rcp_check_kernel(uint32_t first_bits, uint32_t count, unsigned l
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int vote_smem_bytes(int tile_phi, int tile_d, int nk) {
-    return 16 * tile_d + 4 * tile_phi * tile_d * nk;
+int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band) {
+    const int chunk = band ? threads * (4 + 4 + 4 + 2 * kBuckets) + 4 : 0;
+    return 16 * tile_d + chunk + 4 * tile_phi * tile_d * nk;
 }
 
 
@@ -850,6 +1193,29 @@ static cudaError_t prep_one(int smem) {
 template <int S, int N>
 static void* vote_fn() {
     return reinterpret_cast<void*>(vote_kernel<S, N>);
+}
+template <int S, int N>
+static void* vote_band_fn() {
+    return reinterpret_cast<void*>(vote_band_kernel<S, N>);
+}
+
+static void* vote_band_instance(int tile_phi, int nk) {
+#define HT_VOTEB_NK(S)                             \
+    switch (nk) {                                  \
+        case 64: return vote_band_fn<S, 64>();     \
+        case 128: return vote_band_fn<S, 128>();   \
+        case 256: return vote_band_fn<S, 256>();   \
+        case 512: return vote_band_fn<S, 512>();   \
+        default: return vote_band_fn<S, 0>();      \
+    }
+    switch (tile_phi) {
+        case 1: HT_VOTEB_NK(1)
+        case 2: HT_VOTEB_NK(2)
+        case 4: HT_VOTEB_NK(4)
+        case 8: HT_VOTEB_NK(8)
+    }
+#undef HT_VOTEB_NK
+    return nullptr;
 }
 
 // kernel instance for (tile_phi, n_kappa): compile-time n_kappa for the common widths
@@ -872,8 +1238,8 @@ static void* vote_instance(int tile_phi, int nk) {
     return nullptr;
 }
 
-cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks) {
-    void* f = vote_instance(tile_phi, nk);
+cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, bool band) {
+    void* f = band ? vote_band_instance(tile_phi, nk) : vote_instance(tile_phi, nk);
     if (!f) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
 }
@@ -883,15 +1249,16 @@ cudaError_t launch_finalize(int64_t* scal, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t vote_prepare(int tile_phi, int nk, int smem) {
-    void* f = vote_instance(tile_phi, nk);
+cudaError_t vote_prepare(int tile_phi, int nk, int smem, bool band) {
+    void* f = band ? vote_band_instance(tile_phi, nk) : vote_instance(tile_phi, nk);
     if (!f) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s) {
+cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s,
+                        bool band) {
     if (grid <= 0) return cudaSuccess;
-    void* f = vote_instance(tile_phi, p.K.nk);
+    void* f = band ? vote_band_instance(tile_phi, p.K.nk) : vote_instance(tile_phi, p.K.nk);
     if (!f) return cudaErrorInvalidValue;
     void* args[] = {const_cast<VoteParams*>(&p)};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
@@ -973,18 +1340,18 @@ cudaError_t launch_scan(const ScanRange& r, int64_t* scratch, cudaStream_t s) {
 }
 
 template <int S, int N>
-static void* assoc_fn() {
-    return reinterpret_cast<void*>(assoc_kernel<S, N>);
+static void* assoc_fn(bool band) {
+    return band ? reinterpret_cast<void*>(assoc_kernel<S, N, true>) : reinterpret_cast<void*>(assoc_kernel<S, N, false>);
 }
 
-static void* assoc_instance(int tile_phi, int nk) {
-#define HT_ASSOC_NK(S)                         \
-    switch (nk) {                              \
-        case 64: return assoc_fn<S, 64>();     \
-        case 128: return assoc_fn<S, 128>();   \
-        case 256: return assoc_fn<S, 256>();   \
-        case 512: return assoc_fn<S, 512>();   \
-        default: return assoc_fn<S, 0>();      \
+static void* assoc_instance(int tile_phi, int nk, bool band) {
+#define HT_ASSOC_NK(S)                             \
+    switch (nk) {                                  \
+        case 64: return assoc_fn<S, 64>(band);     \
+        case 128: return assoc_fn<S, 128>(band);   \
+        case 256: return assoc_fn<S, 256>(band);   \
+        case 512: return assoc_fn<S, 512>(band);   \
+        default: return assoc_fn<S, 0>(band);      \
     }
     switch (tile_phi) {
         case 1: HT_ASSOC_NK(1)
@@ -996,24 +1363,24 @@ static void* assoc_instance(int tile_phi, int nk) {
     return nullptr;
 }
 
-size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads) {
-    return assoc_smem_bytes(tile_phi, tile_d, nk, threads);
+size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads, bool band) {
+    return assoc_smem_bytes(tile_phi, tile_d, nk, threads, band);
 }
 
-cudaError_t assoc_prepare(int tile_phi, int nk, int smem) {
-    void* f = assoc_instance(tile_phi, nk);
+cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band) {
+    void* f = assoc_instance(tile_phi, nk, band);
     if (!f) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int tile_d, int threads, cudaStream_t s) {
     if ((int64_t)p.n_events * p.K.nphi == 0) return cudaSuccess;
-    void* f = assoc_instance(tile_phi, p.K.nk);
+    void* f = assoc_instance(tile_phi, p.K.nk, p.band != 0);
     if (!f) return cudaErrorInvalidValue;
     const int tiles = ((p.K.nphi + tile_phi - 1) / tile_phi) * ((p.K.nd + tile_d - 1) / tile_d);
     const int64_t items = (int64_t)p.n_events * tiles;
     const int grid = (int)std::min<int64_t>(items, 152 * 32);
-    const int smem = (int)assoc_smem_bytes(tile_phi, tile_d, p.K.nk, threads);
+    const int smem = (int)assoc_smem_bytes(tile_phi, tile_d, p.K.nk, threads, p.band != 0);
     int td = tile_d;
     void* args[] = {const_cast<AssocParams*>(&p), &td};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);

@@ -40,6 +40,7 @@ HT_OPT_PHASE_TIMING = 8
 HT_OPT_LAUNCHES = 9
 HT_OPT_ATILE_PHI = 10
 HT_OPT_ATILE_D0 = 11
+HT_OPT_PRUNE = 12
 HT_MODE_BATCHED = 0
 HT_MODE_PLAIN = 1
 

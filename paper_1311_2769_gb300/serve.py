@@ -37,13 +37,17 @@ class Event:
 
 @dataclasses.dataclass
 class EventResult:
-    eid: int
-    peaks: np.ndarray          # (i_phi, i_d0, i_kappa, votes) rows, ascending
-    offsets: np.ndarray        # int64 [n_peaks + 1] CSR row pointers into hits (from 0)
-    hits: Optional[np.ndarray]  # int32 hit indices within the event, ascending per row
+    """Completion record of one event.  The peak list and CSR rows are in host
+    memory when it is produced; they reach callers through the executor's
+    `consumer(eid, peaks, offsets, hits, hit_base)` callback as views into the
+    slot's pinned buffers, valid only during the callback (copy what you keep):
+    peaks int32 [n, 5] (event, i_phi, i_d0, i_kappa, votes), offsets int64
+    [n + 1] CSR pointers (absolute, subtract offsets[0]), hits int32 batch hit
+    indices (subtract hit_base for indices within the event)."""
 
-    def row(self, p: int) -> np.ndarray:
-        return self.hits[self.offsets[p]:self.offsets[p + 1]]
+    eid: int
+    n_peaks: int
+    n_pairs: int
 
 
 def poisson_trace(rate_hz: float, n_events: int, seed: int = 4, workload: str = "serving_lognormal"):
@@ -146,7 +150,7 @@ class GpuExecutor:
 
     def __init__(self, grid, layer_r, threshold: int, window: int, slots: int = 3, max_batch: int = 512,
                  max_hits: int = 1 << 22, peak_cap: int = 1 << 24, pair_cap: int = 1 << 29, device=None,
-                 copy_hits_back: bool = True):
+                 copy_hits_back: bool = True, consumer=None):
         import torch
 
         from . import ht
@@ -156,6 +160,7 @@ class GpuExecutor:
         self.slots = int(slots)
         self.bytes_per_event = 4 * grid.n_phi * grid.n_d0 * grid.n_kappa
         self.copy_hits_back = copy_hits_back
+        self.consumer = consumer
         self.state = []
         for _ in range(self.slots):
             ctx = ht.Context(grid, layer_r)
@@ -237,11 +242,10 @@ class GpuExecutor:
         out = []
         for b, e in enumerate(st["events"]):
             lo, hi = int(bounds[b]), int(bounds[b + 1])
-            o = off[lo:hi + 1] - off[lo]
-            h = None
-            if hits is not None:
-                h = (hits[off[lo]:off[hi]] - np.int32(offs[b])).astype(np.int32)
-            out.append(EventResult(e.eid, pk[lo:hi, 1:].copy(), o.astype(np.int64), h))
+            if self.consumer is not None:
+                self.consumer(e.eid, pk[lo:hi], off[lo:hi + 1],
+                              None if hits is None else hits[off[lo]:off[hi]], int(offs[b]))
+            out.append(EventResult(e.eid, hi - lo, int(off[hi] - off[lo])))
         st["done"] = None
         return out
 

@@ -146,3 +146,49 @@ def stage2(x, y, c, s, d, K, rcp_err=0.0):
         out[cert] = np.where((kk[cert] >= 0) & (kk[cert] < K["nk"]), kk[cert], -1)
         out[ok & ~inwin] = -1
     return out
+
+
+# ---- d0 band of a (hit, phi row): a superset of the columns where it can vote
+
+def band_consts(grid, d0):
+    """Constants of the band computation (the library's make_consts restated)."""
+    nk = int(grid.n_kappa)
+    kmin, kmax = float(F(grid.kappa_min)), float(F(grid.kappa_max))
+    dk = (kmax - kmin) / nk
+    A = kmin - 2 * dk           # widened by two bins each side
+    B = kmax + 2 * dk
+    d0 = np.asarray(d0, np.float64)
+    return dict(A2=F(A * A), B2=F(B * B), iA=F(1.0 / abs(A)), iB=F(1.0 / B), dfirst=F(d0[0]),
+                idd=F(grid.n_d0 / (float(F(grid.d0_max)) - float(F(grid.d0_min)))), big=F(1e30))
+
+
+def band(x, y, c, s, j0, nj, d0, C):
+    """[jlo, jhi] (inclusive, clipped to the tile [j0, j0 + nj)) in float32; jhi < jlo if empty."""
+    x, y, c, s = (np.asarray(v, F) for v in (x, y, c, s))
+    with np.errstate(all="ignore"):
+        r2 = fma(x, x, y * y)
+        q = fma(y, c, -(x * s))
+        p2 = np.maximum(fma(-q, q, r2), F(0))
+        DA = fma(-C["A2"], p2, F(1))
+        DB = fma(-C["B2"], p2, F(1))
+        sA = np.sqrt(np.maximum(DA, F(0)))
+        sB = np.sqrt(np.maximum(DB, F(0)))
+        # forbidden (a1, a2) where kappa < A, [b1, b2] where kappa > B (empty when D <= 0)
+        a1 = np.where(DA > 0, (C["A2"] * p2) * C["iA"] / (F(1) + sA), C["big"])
+        a2 = np.where(DA > 0, (F(1) + sA) * C["iA"], C["big"])
+        b2 = np.where(DB > 0, -(C["B2"] * p2) * C["iB"] / (F(1) + sB), -C["big"])
+        b1 = np.where(DB > 0, -(F(1) + sB) * C["iB"], -C["big"])
+        ulo = F(d0[j0]) - q
+        uhi = F(d0[j0 + nj - 1]) - q
+        lo = np.where(ulo < b1, ulo, np.where((ulo <= a1) & (uhi > b2), np.maximum(ulo, b2),
+                                             np.where(uhi >= a2, np.maximum(ulo, a2), C["big"])))
+        hi = np.where(uhi >= a2, uhi, np.where((uhi > b2) & (ulo <= a1), np.minimum(uhi, a1),
+                                              np.where(ulo < b1, np.minimum(uhi, b1), -C["big"])))
+        jl = np.floor((lo + q - C["dfirst"]) * C["idd"]) - 1
+        jh = np.floor((hi + q - C["dfirst"]) * C["idd"]) + 2
+        jlo = np.clip(jl, j0, j0 + nj).astype(np.int64)
+        jhi = np.clip(jh, j0 - 1, j0 + nj - 1).astype(np.int64)
+        empty = ~(lo <= hi)
+        jlo = np.where(empty, j0 + nj, jlo)
+        jhi = np.where(empty, j0 - 1, jhi)
+    return jlo, jhi

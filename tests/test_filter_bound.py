@@ -88,3 +88,33 @@ def test_stage1_and_stage2_never_disagree_with_binary64(oracle_mod, wname):
     assert und2 <= 2, und2
     # even among adversarial cells only hits within ~1e-3 cm of a perigee point reach binary64
     assert und2_adv / (x.shape[0] - n0) < 0.7, und2_adv
+
+
+@pytest.mark.parametrize("wname", ["single_event_10trk", "dense_event_500trk", "batch_4096_lognormal",
+                                   "pileup_64x5000trk"])
+def test_d0_band_contains_every_voting_column(oracle_mod, wname):
+    """The pruned vote evaluates only the d0 band of each (hit, phi row); every
+    column where the hit votes in binary64 must lie inside it."""
+    w = synth.WORKLOADS[wname]
+    g = w.grid
+    b = synth.generate(w, n_events=1, first_event=5)
+    c, s, d = oracle_mod.tables(g)
+    C = fm.band_consts(g, d)
+    rng = np.random.default_rng(1)
+    nh = min(600, b.n_hits)
+    hs = rng.choice(b.n_hits, nh, replace=False)
+    rows = rng.choice(g.n_phi, min(64, g.n_phi), replace=False)
+    x = np.repeat(b.x[hs], len(rows))
+    y = np.repeat(b.y[hs], len(rows))
+    ci = np.tile(c[rows], nh)
+    si = np.tile(s[rows], nh)
+    frac = []
+    for j0, nj in ((0, g.n_d0), (0, max(1, g.n_d0 // 2)), (g.n_d0 // 4, max(1, g.n_d0 // 4))):
+        jlo, jhi = fm.band(x, y, ci, si, j0, nj, d, C)
+        for j in range(j0, j0 + nj):
+            k = oracle_mod.kbin_cells(g, x, y, ci, si, np.full(x.shape, d[j], np.float32))
+            votes = k >= 0
+            outside = votes & ((j < jlo) | (j > jhi))
+            assert not outside.any(), (j, np.nonzero(outside)[0][:5])
+        frac.append(np.maximum(jhi - jlo + 1, 0).mean() / nj)
+    assert frac[0] < 0.45, frac

@@ -381,3 +381,73 @@ def test_pileup_events_sampled_columns(ht, oracle_mod):
     po_o, hi_o = oracle_mod.associate(g, b.x, b.y, b.event_offsets, pk_o1[sel], w.window)
     for t, p in enumerate(sel):
         assert np.array_equal(hi[po[base + p]:po[base + p + 1]], hi_o[po_o[t]:po_o[t + 1]])
+
+
+@pytest.mark.parametrize("grid", [synth.Grid(96, 24, 64, -25.0, 25.0, -0.0114, 0.0114),
+                                  synth.Grid(50, 17, 40, -7.0, 30.0, -0.02, 0.005),
+                                  synth.Grid(40, 9, 32, -10.0, 10.0, 0.001, 0.02)])
+def test_pruned_vote_equals_full_vote(ht, oracle_mod, grid):
+    """Voting only each row's d0 band gives the full vote's accumulator
+    (asymmetric ranges; a kappa range that does not straddle 0 disables pruning)."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=3, first_event=21)
+    accs = []
+    for prune in (3, 0):
+        ctx = ht.Context(grid, w.spec.layers)
+        ctx.set_option(ht.HT_OPT_PRUNE, prune)
+        ctx.vote(ht.Hits.from_batch(b, device="cuda"))
+        accs.append([ctx.accumulator(e) for e in range(3)])
+        ctx.close()
+    acc_o = oracle_mod.vote(grid, b.x, b.y, b.event_offsets)
+    for e in range(3):
+        assert np.array_equal(accs[0][e], accs[1][e])
+        assert np.array_equal(accs[0][e], acc_o[e])
+    # association over bands gives the same CSR
+    outs = [_run(ht, grid, b, 4, 1, opts=((ht.HT_OPT_PRUNE, pr),)) for pr in (3, 0)]
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+    pk_o = oracle_mod.peaks(grid, acc_o, 4)
+    assert np.array_equal(outs[0][0], pk_o)
+    _check_csr_rows(oracle_mod, grid, b, *outs[0], 1, 300)
+
+
+@pytest.mark.parametrize("n_phi", [1, 2, 3])
+def test_peaks_with_few_phi_rows(ht, oracle_mod, n_phi):
+    """phi wraps onto the same rows: neighbours coincide (two rows) or are the
+    cell itself (one row); the peak list must still follow the rule."""
+    w = synth.WORKLOADS["single_event_10trk"]
+    b = synth.generate(w, n_events=2)
+    g = synth.Grid(n_phi, 6, 24, -10.0, 10.0, -0.0114, 0.0114)
+    acc_o = oracle_mod.vote(g, b.x, b.y, b.event_offsets)
+    for thr in (1, 3):
+        pk_o = oracle_mod.peaks(g, acc_o, thr)
+        pk, po, hi = _run(ht, g, b, thr, 1)
+        assert np.array_equal(pk, pk_o), (n_phi, thr)
+        po_o, hi_o = oracle_mod.associate(g, b.x, b.y, b.event_offsets, pk_o, 1)
+        assert np.array_equal(po, po_o) and np.array_equal(hi, hi_o)
+
+
+def test_overflow_across_waves(ht):
+    """Caps hit in the first wave: later waves lie wholly past the caps; the
+    stored prefix and the true counts must match an unbounded run."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=6, first_event=300)
+    g = synth.Grid(64, 16, 32, -25.0, 25.0, -0.0114, 0.0114)
+    cells = g.n_phi * g.n_d0 * g.n_kappa
+    full = _run(ht, g, b, 5, 1)
+    for pc, qc in ((50, 400), (len(full[0]) // 3, len(full[2]) // 4)):
+        ctx = ht.Context(g, w.spec.layers)
+        ctx.set_option(ht.HT_OPT_ACC_BUDGET, 2 * cells * 4)
+        res = ht.Results(pc, qc, device="cuda")
+        ctx.process(ht.Hits.from_batch(b, device="cuda"), 5, 1, res)
+        with pytest.raises(ht.HtError) as ei:
+            ctx.sync()
+        assert ei.value.status == ht.HT_ERR_OVERFLOW
+        cnt = res.counts.cpu().numpy()
+        assert cnt[0] == len(full[0]) and cnt[1] == len(full[2])
+        pk, po, hi = res.host()
+        assert np.array_equal(pk, full[0][:pc])
+        n_ok = int(np.searchsorted(po, qc, side="right")) - 1   # rows ending at or below the cap
+        assert np.array_equal(po[: n_ok + 1], full[1][: n_ok + 1])
+        assert np.array_equal(hi[: po[n_ok]], full[2][: po[n_ok]])
+        ctx.close()

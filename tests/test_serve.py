@@ -38,7 +38,7 @@ class FakeExecutor:
         if self.clock() < t_end:
             return None
         del self.running[slot]
-        return [serve.EventResult(e.eid, np.zeros((0, 4), np.int32), np.zeros(1, np.int64), None) for e in evs]
+        return [serve.EventResult(e.eid, 0, 0) for e in evs]
 
 
 def _events(n, rate, seed=0):
@@ -90,15 +90,22 @@ def test_result_same_alone_and_in_the_mix():
     build.build()
     w = synth.WORKLOADS["serving_lognormal"]
     evs = serve.poisson_trace(50000.0, 400, seed=4)
+    rng = np.random.default_rng(0)
+    sample = set(int(v) for v in rng.choice(400, 12, replace=False))
+    kept = {}
+
+    def consumer(eid, peaks, offsets, hits, hit_base):
+        if eid in sample:
+            kept[eid] = (peaks[:, 1:].copy(), (offsets - offsets[0]).copy(), (hits - hit_base).copy())
+
     ex = serve.GpuExecutor(w.grid, w.spec.layers, w.threshold, w.window, slots=3, max_batch=64,
-                           max_hits=1 << 21, peak_cap=1 << 22, pair_cap=1 << 27)
+                           max_hits=1 << 21, peak_cap=1 << 22, pair_cap=1 << 27, consumer=consumer)
     sch = serve.Scheduler(ex, 40 << 30, 64)
     done = sch.run(evs)
     ex.close()
-    assert len(done) == 400 and len(sch.batches) > 3
+    assert len(done) == 400 and len(sch.batches) > 3 and set(kept) == sample
     # alone: each sampled event in a batch of its own
-    rng = np.random.default_rng(0)
-    for eid in rng.choice(400, 12, replace=False):
+    for eid in sorted(sample):
         e = evs[eid]
         ctx = ht.Context(w.grid, w.spec.layers)
         b = synth.from_arrays(e.x, e.y, layer=e.layer)
@@ -107,7 +114,8 @@ def test_result_same_alone_and_in_the_mix():
         ctx.sync()
         pk, po, hi = res.host()
         ctx.close()
-        got = done[int(eid)][0]
+        peaks, offsets, hits = kept[eid]
         want = np.stack([pk["i_phi"], pk["i_d0"], pk["i_kappa"], pk["votes"].astype(np.int32)], 1)
-        assert np.array_equal(got.peaks, want)
-        assert np.array_equal(got.offsets, po) and np.array_equal(got.hits, hi)
+        assert np.array_equal(peaks, want)
+        assert np.array_equal(offsets, po) and np.array_equal(hits, hi)
+        assert done[eid][0].n_peaks == len(pk) and done[eid][0].n_pairs == len(hi)
