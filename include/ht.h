@@ -103,7 +103,7 @@ typedef struct {
  * Peaks beyond peak_cap and pairs beyond pair_cap are dropped and the call
  * reports HT_ERR_OVERFLOW (at ht_sync for device outputs): the first
  * peak_cap peaks and every CSR row that ends at or below pair_cap are still
- * exact; the one row that crosses pair_cap holds an unspecified subset of its
+ * exact; the one row that crosses pair_cap holds the first (lowest) of its
  * hits in its slots below the cap.  Re-run with larger caps for the rest. */
 typedef struct {
     ht_peak *peaks;
@@ -125,8 +125,10 @@ typedef struct {
 #define HT_OPT_USE_GRAPH 7         /* 1 = replay the batched step as a CUDA graph (default 1) */
 #define HT_OPT_PHASE_TIMING 8      /* 1 = time vote / peaks+association with device events */
 #define HT_OPT_LAUNCHES 9          /* read-only: kernels launched by the last ht_process */
-#define HT_OPT_ATILE_PHI 10        /* phi0 rows per association tile: 1, 2, 4 or 8 (0 = auto) */
-#define HT_OPT_ATILE_D0 11         /* d0 columns per association tile (0 = auto) */
+#define HT_OPT_ATILE_PHI 10        /* phi0 rows per association item: 1, 2, 4 or 8 (0 = auto);
+                                      more than 1 only with HT_OPT_ATILE_D0 = n_d0 */
+#define HT_OPT_ATILE_D0 11         /* d0 columns per association item (0 = auto); rows x
+                                      columns of an item at most 32 */
 #define HT_OPT_PRUNE 12            /* bit 0: the vote, bit 1: the association walk only each (hit,
                                       phi0) row's d0 band that can hold a vote (a proven superset)
                                       instead of every cell; same results.  Default 0. */

@@ -74,8 +74,8 @@ struct ht_ctx {
     // options
     int mode = HT_MODE_BATCHED;
     int tile_phi = 0, tile_d = 0, threads = 0;
-    int atile_phi = 0, atile_d = 0;  // association tile (0 = auto)
-    int prune = 0;                   // bit 0: vote, bit 1: association walk only d0 bands
+    int atile_phi = 0, atile_d = 0;  // association item (0 = auto)
+    int prune = 0;                   // bit 0: vote, bit 1: association evaluate only d0 bands
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
@@ -83,7 +83,8 @@ struct ht_ctx {
     // resolved tile configuration
     int r_tile_phi = 1, r_tile_d = 1, r_threads = 256, r_smem = 0, r_blocks_per_sm = 1;
     bool r_band = false, a_band = false;
-    int a_tile_phi = 1, a_tile_d = 1, a_threads = 256, a_smem = 0;  // association tile
+    int a_tile_phi = 1, a_tile_d = 1, a_threads = 256, a_cap = 0, a_blocks_per_sm = 1;  // association item
+    size_t a_warp_bytes = 0;
 
     int gen = 0;  // buffer generation (graph invalidation)
     DBuf<float> sx, sy;
@@ -102,7 +103,8 @@ struct ht_ctx {
     DBuf<int64_t> scratch;
     int64_t* d_scal = nullptr;  // [0] peak total [1] pair total [2] wave peak base [3] wave pair base [4] extra pairs
     int32_t* d_err = nullptr;   // validation bits
-    int32_t* d_queue = nullptr; // persistent vote queue
+    int32_t* d_queue = nullptr; // persistent vote queue (int32) and association queue (u64 at byte 8)
+    unsigned long long* d_aqueue = nullptr;
     unsigned long long* d_stats = nullptr;
     int64_t* h_pinned = nullptr;  // pinned mirror of a few scalars
 
@@ -275,21 +277,58 @@ int resolve_tiles(ht_ctx* ctx) {
     ctx->r_threads = thr;
     ctx->r_smem = smem;
     ctx->r_blocks_per_sm = per_sm;
-    // association tile: its own phi rows and d0 width (default 4 x 16), the
-    // width halved until metadata, write cursors, queues and sort buffers fit
-    // in 200 KB of shared memory
-    const int atp = ctx->atile_phi > 0 ? std::min(ctx->atile_phi, 8) : std::min(4, ctx->grid.n_phi >= 4 ? 4 : 1);
-    int atd = ctx->atile_d > 0 ? std::min(ctx->atile_d, nd) : std::min(nd, 16);
+    // association items: a_tile_phi rows x a_tile_d d0 columns, at most 32
+    // columns, several rows only over all d0 columns (so an item's peaks are
+    // consecutive).  Per warp: the d0 table, the item's peak tables and row
+    // cursors, within 9 KB (three 8-warp blocks per SM) where possible.
+    // Default: 32 d0 columns of one row, or as many whole rows as fit in 32
+    // columns, fewer columns while the tables and 256 cursors exceed 9 KB;
+    // then as many cursors as fit, 256 to 1024.
+    const int nphi = ctx->grid.n_phi;
+    constexpr size_t kWarpBudget = 9216;
+    auto fits = [&](int rows, int cols) { return assoc_warp_smem(rows, cols, nk, 256) <= kWarpBudget; };
+    int atp = ctx->atile_phi, atd = ctx->atile_d;
+    if (atp == 0 && atd == 0) {
+        atp = 1;
+        if (nd >= 32) {
+            atd = 32;
+        } else {
+            atd = nd;
+            for (int c : {8, 4, 2})
+                if (c * nd <= 32 && c <= nphi && fits(c, nd)) {
+                    atp = c;
+                    break;
+                }
+        }
+        if (atp == 1)
+            while (atd > 1 && !fits(1, atd)) atd = (atd + 1) / 2;
+    } else if (atp == 0) {
+        atp = 1;
+    } else if (atd == 0) {
+        atd = atp > 1 ? nd : std::min(nd, 32);
+    }
+    atd = std::min(atd, nd);
+    if (atp * atd > 32 || (atp > 1 && atd != nd))
+        return fail(ctx, HT_ERR_INVALID_ARG,
+                    "association item %d x %d: at most 32 columns, and more than one row needs all %d d0 columns",
+                    atp, atd, nd);
     const int athr = std::min(thr, 256);
     const bool aband = ctx->a_band;
-    while (atd > 1 && assoc_smem(atp, atd, nk, athr, aband) > 200 * 1024) atd = (atd + 1) / 2;
-    const int asmem = (int)assoc_smem(atp, atd, nk, athr, aband);
-    if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association tile does not fit shared memory");
-    CU(assoc_prepare(atp, nk, asmem, aband));
+    const size_t fixed = assoc_warp_smem(atp, atd, nk, 0);
+    int cap = fixed + 4 * 256 <= kWarpBudget ? (int)((kWarpBudget - fixed) / 4) & ~31 : 256;
+    cap = std::min(cap, 1024);
+    const size_t wbytes = assoc_warp_smem(atp, atd, nk, cap);
+    const int asmem = (int)(wbytes * (athr / 32));
+    if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association item does not fit shared memory");
+    int ablocks = 0;
+    CU(assoc_prepare(atp, nk, asmem, aband, athr, &ablocks));
+    if (ablocks < 1) return fail(ctx, HT_ERR_INVALID_ARG, "association kernel cannot launch");
     ctx->a_tile_phi = atp;
     ctx->a_tile_d = atd;
     ctx->a_threads = athr;
-    ctx->a_smem = asmem;
+    ctx->a_cap = cap;
+    ctx->a_warp_bytes = wbytes;
+    ctx->a_blocks_per_sm = ablocks;
     return HT_OK;
 }
 
@@ -442,9 +481,45 @@ int run_detect_scan(ht_ctx* ctx, const PeakParams& pp, cudaStream_t s) {
     return HT_OK;
 }
 
+// Association of events [event0, event0 + ne) (their peaks numbered from the
+// column bases): the item-layout fields, a zeroed work counter, a grid of
+// resident blocks.
+int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, const int32_t* order,
+                     cudaStream_t s) {
+    a.x = ctx->cx;
+    a.y = ctx->cy;
+    a.offs = ctx->coffs;
+    a.n_hits = ctx->c_hits;
+    a.event0 = event0;
+    a.n_events = ne;
+    a.mask = ctx->mask.p;
+    a.wpre = ctx->wpre.p;
+    a.npk = ctx->npk.p;
+    a.colbase = ctx->colbase.p;
+    a.band = ctx->a_band ? 1 : 0;
+    a.wd = ctx->a_tile_d;
+    a.cap = ctx->a_cap;
+    a.warp_bytes = ctx->a_warp_bytes;
+    a.order = order;
+    a.queue = ctx->d_aqueue;
+    a.cphi = ctx->d_cphi;
+    a.sphi = ctx->d_sphi;
+    a.dtab = ctx->d_dtab;
+    a.K = ctx->K;
+    a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+    const int64_t items = (int64_t)ne * ((ctx->grid.n_phi + ctx->a_tile_phi - 1) / ctx->a_tile_phi) *
+                          ((ctx->grid.n_d0 + ctx->a_tile_d - 1) / ctx->a_tile_d);
+    const int warps = ctx->a_threads / 32;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((items + warps - 1) / warps, (int64_t)ctx->sms * ctx->a_blocks_per_sm));
+    CU(cudaMemsetAsync(ctx->d_aqueue, 0, sizeof(unsigned long long), s));
+    CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_threads, grid, s));
+    return HT_OK;
+}
+
 // pair offsets for this wave's peaks [d_scal[2], d_scal[0]) clamped to cap, and association
-int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, int64_t* peak_offsets,
-                    int32_t* hit_idx, int64_t pair_cap, int32_t window, cudaStream_t s) {
+int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* order, int64_t peak_cap,
+                    int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, cudaStream_t s) {
     CU(cudaMemcpyAsync(ctx->d_scal + 3, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     ScanRange r{};
     r.in = ctx->paircnt.p;
@@ -457,29 +532,12 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, int64_t peak_cap, i
     r.write_end = 1;
     CU(launch_scan(r, ctx->scratch.p, s));
     AssocParams a{};
-    a.x = ctx->cx;
-    a.y = ctx->cy;
-    a.offs = ctx->coffs;
-    a.n_hits = ctx->c_hits;
-    a.event0 = event0;
-    a.n_events = ne;
-    a.mask = ctx->mask.p;
-    a.wpre = ctx->wpre.p;
-    a.npk = ctx->npk.p;
-    a.colbase = ctx->colbase.p;
     a.peak_offsets = peak_offsets;
     a.peak_cap = peak_cap;
     a.hit_idx = hit_idx;
     a.pair_cap = pair_cap;
     a.window = window;
-    a.band = ctx->a_band ? 1 : 0;
-    a.cphi = ctx->d_cphi;
-    a.sphi = ctx->d_sphi;
-    a.dtab = ctx->d_dtab;
-    a.K = ctx->K;
-    a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
-    CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
-    return HT_OK;
+    return launch_assoc_ctx(ctx, a, event0, ne, order, s);
 }
 
 // The legacy default stream cannot be captured into a graph; a caller's NULL
@@ -528,7 +586,8 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
         st = run_detect_scan(ctx, pp, s);
         if (st) return st;
         CU(launch_emit(pp, s));
-        st = run_pairs_assoc(ctx, e0, ne, peak_cap, peak_offsets, hit_idx, pair_cap, window, s);
+        st = run_pairs_assoc(ctx, e0, ne, plain ? nullptr : ctx->order.p, peak_cap, peak_offsets, hit_idx, pair_cap,
+                             window, s);
         if (st) return st;
         if (single && (st = mark(ctx, 2, s))) return st;
         ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1;
@@ -612,7 +671,7 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
         bad(cudaMalloc(&ctx->d_sphi, grid->n_phi * sizeof(float))) ||
         bad(cudaMalloc(&ctx->d_dtab, grid->n_d0 * sizeof(float4))) ||
         bad(cudaMalloc(&ctx->d_scal, 8 * sizeof(int64_t))) || bad(cudaMalloc(&ctx->d_err, sizeof(int32_t))) ||
-        bad(cudaMalloc(&ctx->d_queue, sizeof(int32_t))) || bad(cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long))) ||
+        bad(cudaMalloc(&ctx->d_queue, 16)) || bad(cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long))) ||
         bad(cudaMallocHost(&ctx->h_pinned, 8 * sizeof(int64_t))) ||
         bad(cudaMemcpy(ctx->d_cphi, ctx->h_cphi.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
         bad(cudaMemcpy(ctx->d_sphi, ctx->h_sphi.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
@@ -622,6 +681,7 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
         ht_destroy(ctx);
         return st;
     }
+    ctx->d_aqueue = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->d_queue) + 8);
     st = resolve_tiles(ctx);
     if (st) {
         ht_destroy(ctx);
@@ -831,28 +891,13 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     const int64_t total = ctx->h_pinned[1];
     CU(ctx->hitidx.ensure(std::max<int64_t>(total, 1), &ctx->gen));
     AssocParams a{};
-    a.x = ctx->cx;
-    a.y = ctx->cy;
-    a.offs = ctx->coffs;
-    a.n_hits = ctx->c_hits;
-    a.event0 = 0;
-    a.n_events = ctx->c_events;
-    a.mask = ctx->mask.p;
-    a.wpre = ctx->wpre.p;
-    a.npk = ctx->npk.p;
-    a.colbase = ctx->colbase.p;
     a.peak_offsets = ctx->peakoff.p;
     a.peak_cap = np;
     a.hit_idx = ctx->hitidx.p;
     a.pair_cap = total;
     a.window = window;
-    a.band = ctx->a_band ? 1 : 0;
-    a.cphi = ctx->d_cphi;
-    a.sphi = ctx->d_sphi;
-    a.dtab = ctx->d_dtab;
-    a.K = ctx->K;
-    a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
-    CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_tile_d, ctx->a_threads, s));
+    const int st = launch_assoc_ctx(ctx, a, 0, ctx->c_events, nullptr, s);
+    if (st) return st;
     CU(cudaMemcpyAsync(peak_offsets, ctx->peakoff.p, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     const int64_t ncopy = std::min(total, cap);
     if (ncopy > 0) CU(cudaMemcpyAsync(hit_idx, ctx->hitidx.p, ncopy * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -914,6 +959,8 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         key.vals[8] = ctx->r_tile_phi * 100000 + ctx->r_tile_d;
         key.vals[9] = ctx->r_threads;
         key.vals[10] = ctx->count_stages * 2 + ctx->timing;
+        key.vals[11] = ((int64_t)ctx->a_tile_phi << 40) | ((int64_t)ctx->a_tile_d << 20) | ((int64_t)ctx->a_cap << 2) |
+                       (ctx->r_band ? 2 : 0) | (ctx->a_band ? 1 : 0);
         if (!ctx->gvalid || !(key == ctx->gkey)) {
             if (ctx->gexec) {
                 cudaGraphExecDestroy(ctx->gexec);

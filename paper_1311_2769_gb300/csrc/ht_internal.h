@@ -62,7 +62,12 @@ struct AssocParams {
     int32_t* hit_idx;
     int64_t pair_cap;
     int32_t window;
-    int32_t band;           // 1: walk each (hit, row)'s d0 band only
+    int32_t band;           // 1: evaluate only the d0 columns inside some lane's band
+    int32_t wd;             // d0 columns per item (tile_phi * wd <= 32; tile_phi > 1 needs wd == n_d0)
+    int32_t cap;            // row cursors per warp
+    size_t warp_bytes;      // shared memory per warp
+    const int32_t* order;   // wave-local event order (largest first) or nullptr
+    unsigned long long* queue;  // work counter, zeroed before the launch
     const float* cphi;
     const float* sphi;
     const float4* dtab;
@@ -105,9 +110,9 @@ cudaError_t launch_emit(const PeakParams& p, cudaStream_t s);
 cudaError_t launch_paircount(const PeakParams& p, const int64_t* lo_dev, const int64_t* hi_dev,
                              cudaStream_t s);
 cudaError_t launch_scan(const ScanRange& r, int64_t* scratch /* 2 * kScanBlocks */, cudaStream_t s);
-size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads, bool band);
-cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band);
-cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int tile_d, int threads, cudaStream_t s);
+size_t assoc_warp_smem(int rows, int wd, int nk, int cap);
+cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band, int threads, int* blocks_per_sm);
+cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int grid, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
 
 }  // namespace ht

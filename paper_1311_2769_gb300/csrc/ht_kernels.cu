@@ -717,390 +717,194 @@ __global__ void scan_down_kernel(const ScanRange r, const int64_t* partial, int 
 }
 
 // ---------------------------------------------------------------------------
-// association: the vote's tiling again.  A CTA owns a (phi0, d0) tile of one
-// event, loads the tile's peak bitmasks, marks the kappa bins that lie within
-// `window` of a peak ("near" bits), and streams the event's hits through the
-// same certified binning as the vote.  A hit whose bin is near a peak is
-// appended to each such peak's CSR row through a shared-memory cursor; rows
-// are then put in ascending hit order (most already are) by a warp rank sort.
+// association: rows in hit order, one warp per item.  An item is SPHI phi
+// rows x up to `wd` d0 columns of one event (at most 32 columns; SPHI > 1
+// only with wd == n_d0, so the item's columns, and therefore its peaks, are
+// consecutive in the peak numbering).  The warp loads the item's peak
+// bitmasks, marks the kappa bins within `window` of a peak ("near" bits) and
+// walks the event's hits 32 at a time in increasing order through the same
+// certified binning as the vote.  Cells whose bin is near a peak enter a
+// per-warp FIFO ring by ballot rank, so for every column the ring holds hits
+// in increasing order.  A drain hands 32 entries to the 32 lanes, which rank
+// themselves among the lanes holding the same peak (a match over peak ids);
+// one lane per peak moves the row's cursor.  A row is written by one warp
+// only, drain after drain, so it comes out in ascending hit order with no
+// atomics and no sort.  Cursors live in shared memory, `cap` per warp; an
+// item with more peaks is walked once per block of `cap` peaks.
 // ---------------------------------------------------------------------------
-constexpr int kSortCap = 1024;  // per-warp shared sort buffer (hit indices)
-constexpr int kQueue = 64;      // per-warp candidate queue (drained at >= 32)
+// Columns per step of the cell loop (each with SPHI rows), and the ring
+// size: a step pushes at most 32 entries per cell on top of < 32 waiting.
+__host__ __device__ constexpr int assoc_unroll(int sphi) { return sphi >= 2 ? 1 : 2; }
+__host__ __device__ constexpr int assoc_ring(int sphi) {
+    int r = 64;
+    while (r < 32 * (assoc_unroll(sphi) * sphi + 1)) r <<= 1;
+    return r;
+}
 
-struct AssocSmem {
-    float4* dt;        // [tile_d]
-    uint32_t* mask;    // [tile_cols][nkw] peak bits
-    uint32_t* nearb;   // [tile_cols][nkw] near-peak bits
-    int32_t* lpre;     // [tile_cols][nkw] first local peak slot of the word
-    int64_t* gpre;     // [tile_cols][nkw] first global peak id of the word
-    unsigned long long* wpos;  // [tile_cols * ceil(nk/2)] next CSR write position per local peak
-    uint2* queue;      // [warps][kQueue] (column << 16 | kappa bin, hit)
-    int32_t* sortbuf;  // [warps][kSortCap]
-    int32_t* active;   // [tile_d] d0 columns of the tile holding any peak
-    float* sx;         // [threads] band bucketing records of the current hit chunk
-    float* sy;
-    int* sband;
-    uint16_t* slist;   // [kBuckets][threads]
-    int* cnt;          // [kBuckets] bucket fill counts
+struct AssocWarp {
+    float4* dt;      // [wd] d0 table of the item's columns
+    uint32_t* cur;   // [cap] row cursors of the pass's peaks (offsets from the pass's first row)
+    uint2* ring;     // [assoc_ring(rows)] (column << 16 | kappa bin, hit)
+    uint32_t* mask;  // [rows * wd][nkw] peak bits of the item's columns
+    uint32_t* nearb; // [rows * wd][nkw] bins within `window` of a peak
+    int32_t* lpre;   // [rows * wd][nkw] item-local id of the first peak of each word
 };
 
-__host__ __device__ inline size_t assoc_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band) {
-    const size_t cols = (size_t)tile_phi * tile_d, nkw = (nk + 31) / 32;
-    return 16 * (size_t)tile_d + cols * nkw * (4 + 4 + 4 + 8) + cols * ((nk + 1) / 2) * 8 +
-           (size_t)(threads / 32) * (kQueue * 8 + kSortCap * 4) + 4 * (size_t)tile_d +
-           (band ? (size_t)threads * (4 + 4 + 4 + 2 * kBuckets) : 0) + 64;
+__host__ __device__ inline size_t assoc_warp_bytes(int rows, int wd, int nk, int cap) {
+    const size_t nkw = (nk + 31) / 32;
+    return ((16 * (size_t)wd + 4 * (size_t)cap + 8 * (size_t)assoc_ring(rows) + 12 * (size_t)rows * wd * nkw) +
+            15) &
+           ~size_t(15);
 }
 
-// One queued candidate (column c of the tile, kappa bin kb, hit h): append h
-// to every peak within `window` bins of kb.
-__device__ __forceinline__ void assoc_append(const AssocParams& p, const AssocSmem& S, int nkw, int nk, uint2 ent) {
+struct AssocPass {
+    int L0, L1;     // item-local peak ids of this pass
+    bool whole;     // the pass holds all of the item's stored peaks
+    int64_t Q;      // first row offset of the pass
+};
+
+// Rows of the n (<= 32) ring entries from `head`, lane i taking entry i.  An
+// entry's peaks lie within `window` of its bin and at least two bins apart
+// (a peak is strictly above its lower kappa neighbour and not below its
+// upper one), so the peak at bin k can be given round (k >> 1) mod R, R the
+// power of two >= window + 1: no entry has two peaks in one round, and every
+// entry holding a given peak meets it in the same round.  In a round, lanes
+// with equal peaks match; each takes its rank among them (lane order, which
+// is hit order for a column) and the group's lowest lane moves the row's
+// cursor.  When no entry holds two peaks, one round over all of them does.
+template <int RING>
+__device__ __forceinline__ void assoc_drain(const AssocParams& p, const AssocWarp& S, int nkw, int nk, unsigned head,
+                                            int n, const AssocPass& ps, int lane) {
+    __syncwarp();
+    const bool has = lane < n;
+    const uint2 ent = has ? S.ring[(head + lane) & (RING - 1)] : make_uint2(0u, 0u);
     const int c = (int)(ent.x >> 16), kb = (int)(ent.x & 0xFFFFu);
-    for (int o = -p.window; o <= p.window; ++o) {
-        const int kk = kb + o;
-        if (kk < 0 || kk >= nk) continue;
-        const int wd = kk >> 5;
-        const uint32_t bits = S.mask[c * nkw + wd];
-        if (!((bits >> (kk & 31)) & 1u)) continue;
-        const int below = __popc(bits & ((1u << (kk & 31)) - 1u));
-        const int64_t pid = S.gpre[c * nkw + wd] + below;
-        if (pid >= p.peak_cap) continue;
-        const unsigned long long pos = atomicAdd(&S.wpos[S.lpre[c * nkw + wd] + below], 1ull);
-        if ((int64_t)pos < p.pair_cap) p.hit_idx[pos] = (int32_t)ent.y;
-    }
-}
-
-// Push this lane's candidate (if any) into the warp queue; drain 32 at a time.
-__device__ __forceinline__ void queue_push(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn, int nkw,
-                                           int nk, bool cand, uint2 ent, int lane) {
-    const unsigned m = __ballot_sync(0xffffffffu, cand);
-    if (!m) return;
-    if (cand) q[qn + __popc(m & lanemask_lt())] = ent;
-    qn += __popc(m);
-    if (qn >= 32) {
-        __syncwarp();
-        assoc_append(p, S, nkw, nk, q[qn - 32 + lane]);
-        __syncwarp();
-        qn -= 32;
-    }
-}
-
-__device__ __forceinline__ void queue_drain(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn, int nkw,
-                                            int nk, int lane) {
-    __syncwarp();
-    if (lane < qn) assoc_append(p, S, nkw, nk, q[lane]);
-    __syncwarp();
-    qn = 0;
-}
-
-template <int SPHI, int NK, bool TAIL>
-__device__ __forceinline__ void assoc_one_hit(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn,
-                                              const float* cp, const float* sp, int n_active, int nk, int nkw,
-                                              int64_t h, bool valid, int lane) {
-    const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
-    const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
-    const HitFast hf = hit_fast(x, y, p.K);
-    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
-    float q_[SPHI], qs[SPHI];
-#pragma unroll
-    for (int r = 0; r < SPHI; ++r) {
-        q_[r] = q_of(x, y, cp[r], sp[r]);
-        qs[r] = q_[r] * S2;
-    }
-    const unsigned nku = (unsigned)nk;
-    for (int ja = 0; ja < n_active; ++ja) {
-        const int j = S.active[ja];
-        const float4 dt = S.dt[j];
-        const float Rj = hf.r2 + dt.z;
-        bool und = false;
-#pragma unroll
-        for (int r = 0; r < SPHI; ++r) {
-            const int c = j * SPHI + r;
-            const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
-            bool vote = (o.flo == o.fhi) & (o.kb < nku);
-            if (TAIL) vote &= valid;
-            // kb is only meaningful (< n_kappa) when vote; other lanes read word 0
-            const uint32_t nb = S.nearb[c * nkw + (vote ? (o.kb >> 5) : 0u)];
-            const bool cand = vote && ((nb >> (o.kb & 31)) & 1u);
-            queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | o.kb, (unsigned)h), lane);
-            und |= (o.flo != o.fhi) & (!TAIL || valid);
-        }
-        if (__any_sync(0xffffffffu, und)) {
-#pragma unroll
-            for (int r = 0; r < SPHI; ++r) {
-                const int c = j * SPHI + r;
-                const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
-                int kk = -1;
-                if ((o.flo != o.fhi) && (!TAIL || valid) && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi))
-                    kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
-                const bool cand = kk >= 0 && ((S.nearb[c * nkw + (kk >> 5)] >> (kk & 31)) & 1u);
-                queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | (unsigned)kk, (unsigned)h),
-                           lane);
+    const int w = p.window;
+    const int k0 = kb - w;
+    // pending: the peaks of column c (of this pass) at k0 + rel, rel in [0, 2w]
+    unsigned pend = 0;
+    if (has) {
+        const uint32_t* m = S.mask + c * nkw;
+        const int lo = max(k0, 0), hi = min(kb + w, nk - 1);
+        const int a = lo >> 5, b = hi >> 5;  // b <= a + 1 since 2w < 32
+        const unsigned long long two =
+            ((unsigned long long)(b > a ? m[b] : 0u) << 32) | (unsigned long long)m[a];
+        const unsigned span = (unsigned)(two >> (lo & 31)) & (0xFFFFFFFFu >> (31 - (hi - lo)));
+        pend = span << (lo - k0);
+        if (!ps.whole) {
+            for (unsigned bits = pend; bits; bits &= bits - 1u) {
+                const int rel = __ffs(bits) - 1;
+                const int kk = k0 + rel;
+                const uint32_t word = m[kk >> 5];
+                const int local = S.lpre[c * nkw + (kk >> 5)] + __popc(word & ((1u << (kk & 31)) - 1u));
+                if (local < ps.L0 || local >= ps.L1) pend &= ~(1u << rel);
             }
         }
     }
-}
-
-// Association over d0 bands: the vote's bucketing (see vote_band_kernel),
-// bands clipped to the tile's columns [ja, ja + nja) that hold peaks.
-template <int SPHI, int NK>
-__device__ __forceinline__ void assoc_band_hits(const AssocParams& p, const AssocSmem& S, uint2* q, int& qn,
-                                                const float* cp, const float* sp, int ja, int nja, int j0,
-                                                int nrows, int nk, int nkw, int64_t hb, int64_t he, int lane) {
-    const int nthr = blockDim.x, tid = threadIdx.x, warp = tid >> 5, nw = nthr >> 5;
-    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
-    const unsigned nku = (unsigned)nk;
-    const float dlo = S.dt[ja - j0].x, dhi = S.dt[ja - j0 + nja - 1].x;
-    int lim[kBuckets];
-    lim[0] = max(1, nja / 8);
-    lim[1] = max(1, nja / 4);
-    lim[2] = max(1, nja / 2);
-    lim[3] = nja;
-    for (int64_t cb = hb; cb < he; cb += nthr) {
-        if (tid < kBuckets) S.cnt[tid] = 0;
-        __syncthreads();
-        const int64_t h = cb + tid;
-        int jlo = ja + nja, jhi = ja - 1;
-        float x = 0.0f, y = 0.0f;
-        if (h < he) {
-            x = p.x[h];
-            y = p.y[h];
-            const float r2 = fmaf(x, x, __fmul_rn(y, y));
-#pragma unroll
-            for (int r = 0; r < SPHI; ++r) {
-                if (r >= nrows) break;
-                int a, b;
-                d0_band(r2, q_of(x, y, cp[r], sp[r]), dlo, dhi, ja, nja, p.K, a, b);
-                if (b >= a) {
-                    jlo = min(jlo, a);
-                    jhi = max(jhi, b);
-                }
-            }
+    const unsigned lt = lanemask_lt();
+    const bool multi = __any_sync(0xffffffffu, (pend & (pend - 1u)) != 0u);
+    int R = 1;
+    if (multi)
+        while (R < w + 1) R <<= 1;
+    for (int s = 0; s < R; ++s) {
+        int loc = -1;  // this lane's peak of round s, id within the pass
+        for (unsigned bits = pend; bits; bits &= bits - 1u) {
+            const int rel = __ffs(bits) - 1;
+            const int kk = k0 + rel;
+            if (multi && (((kk >> 1) & (R - 1)) != s)) continue;
+            const uint32_t word = S.mask[c * nkw + (kk >> 5)];
+            loc = S.lpre[c * nkw + (kk >> 5)] + __popc(word & ((1u << (kk & 31)) - 1u)) - ps.L0;
+            break;
         }
-        const int len = jhi >= jlo ? jhi - jlo + 1 : 0;
-        S.sx[tid] = x;
-        S.sy[tid] = y;
-        S.sband[tid] = (jlo - j0) | (len << 16);
-#pragma unroll
-        for (int bk = 0; bk < kBuckets; ++bk) {
-            const bool in = len > 0 && len <= lim[bk] && (bk == 0 || len > lim[bk - 1]);
-            const unsigned m = __ballot_sync(0xffffffffu, in);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(&S.cnt[bk], __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (in) S.slist[bk * nthr + base + __popc(m & lanemask_lt())] = (uint16_t)tid;
+        if (!__any_sync(0xffffffffu, loc >= 0)) continue;
+        const unsigned key = loc >= 0 ? (unsigned)loc : (0x80000000u | (unsigned)lane);
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(grp) - 1;
+        uint32_t base = 0;
+        if (loc >= 0 && lane == leader) {  // the only lane touching this row's cursor in this drain
+            base = S.cur[loc];
+            S.cur[loc] = base + (uint32_t)__popc(grp);
         }
-        __syncthreads();
-        int groups = 0;
-        int gstart[kBuckets + 1];
-#pragma unroll
-        for (int bk = 0; bk < kBuckets; ++bk) {
-            gstart[bk] = groups;
-            groups += (S.cnt[bk] + 31) >> 5;
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (loc >= 0) {
+            const int64_t pos = ps.Q + (int64_t)base + __popc(grp & lt);
+            if (pos < p.pair_cap) p.hit_idx[pos] = (int32_t)ent.y;
         }
-        gstart[kBuckets] = groups;
-        for (int g = warp; g < groups; g += nw) {
-            int bk = 0;
-#pragma unroll
-            for (int b2 = 1; b2 < kBuckets; ++b2) bk += g >= gstart[b2];
-            const int idx = (g - gstart[bk]) * 32 + lane;
-            const bool has = idx < S.cnt[bk];
-            const int ht = has ? S.slist[bk * nthr + idx] : 0;
-            const int bd = has ? S.sband[ht] : 0;
-            const int jl = bd & 0xFFFF, ln = bd >> 16;
-            const float hx = S.sx[ht], hy = S.sy[ht];
-            const int64_t hh = cb + ht;
-            const HitFast hf = hit_fast(hx, hy, p.K);
-            float q_[SPHI], qs[SPHI];
-#pragma unroll
-            for (int r = 0; r < SPHI; ++r) {
-                q_[r] = q_of(hx, hy, cp[r], sp[r]);
-                qs[r] = q_[r] * S2;
-            }
-            const int steps = __reduce_max_sync(0xffffffffu, ln);
-            for (int s = 0; s < steps; ++s) {
-                const bool live = s < ln;
-                const int j = live ? jl + s : ja - j0;
-                const float4 dt = S.dt[j];
-                const float Rj = hf.r2 + dt.z;
-                bool und = false;
-#pragma unroll
-                for (int r = 0; r < SPHI; ++r) {
-                    const int c = j * SPHI + r;
-                    const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
-                    const bool vote = live & (o.flo == o.fhi) & (o.kb < nku);
-                    const uint32_t nb = S.nearb[c * nkw + (vote ? (o.kb >> 5) : 0u)];
-                    const bool cand = vote && ((nb >> (o.kb & 31)) & 1u);
-                    queue_push(p, S, q, qn, nkw, nk, cand, make_uint2(((unsigned)c << 16) | o.kb, (unsigned)hh), lane);
-                    und |= (o.flo != o.fhi) & live;
-                }
-                if (__any_sync(0xffffffffu, und)) {
-#pragma unroll
-                    for (int r = 0; r < SPHI; ++r) {
-                        const int c = j * SPHI + r;
-                        const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
-                        int kk = -1;
-                        if ((o.flo != o.fhi) && live && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi))
-                            kk = cell_slow(hx, hy, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
-                        const bool cand = kk >= 0 && ((S.nearb[c * nkw + (kk >> 5)] >> (kk & 31)) & 1u);
-                        queue_push(p, S, q, qn, nkw, nk, cand,
-                                   make_uint2(((unsigned)c << 16) | (unsigned)kk, (unsigned)hh), lane);
-                    }
-                }
-            }
-        }
-        __syncthreads();
     }
-}
-
-// Ascending order of one CSR row (distinct hit indices) by rank sort.
-__device__ void sort_row(int32_t* seg, int n, int32_t* buf, int lane) {
-    if (n <= 1) return;
-    if (n > kSortCap) {  // rare: long rows sorted in place by one lane
-        if (lane == 0) {
-            for (int a = 1; a < n; ++a) {
-                const int32_t v = seg[a];
-                int b = a - 1;
-                while (b >= 0 && seg[b] > v) {
-                    seg[b + 1] = seg[b];
-                    --b;
-                }
-                seg[b + 1] = v;
-            }
-        }
-        __syncwarp();
-        return;
-    }
-    bool unsorted = false;
-    for (int t = lane; t < n; t += 32) {
-        buf[t] = seg[t];
-        if (t + 1 < n) unsorted |= seg[t] > seg[t + 1];
-    }
-    if (!__any_sync(0xffffffffu, unsorted)) return;
-    __syncwarp();
-    for (int t = lane; t < n; t += 32) {
-        const int32_t v = buf[t];
-        int rank = 0;
-        for (int u = 0; u < n; ++u) rank += buf[u] < v;
-        seg[rank] = v;
-    }
-    __syncwarp();
+    __syncwarp();  // entries read before the ring slots are reused
 }
 
 template <int SPHI, int NK, bool BAND>
-__global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, const int tile_d) {
+__global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = NK ? NK : p.K.nk;
     const int nkw = (nk + 31) >> 5;
-    const int tcols = SPHI * tile_d;
-    const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-    AssocSmem S;
+    const int WD = p.wd;
+    const int ncols = SPHI * WD;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int U = assoc_unroll(SPHI);
+    constexpr int RING = assoc_ring(SPHI);
+    AssocWarp S;
     {
-        unsigned char* ptr = smem_raw;
+        unsigned char* ptr = smem_raw + (size_t)warp * p.warp_bytes;
         S.dt = reinterpret_cast<float4*>(ptr);
-        ptr += 16 * tile_d;
-        S.gpre = reinterpret_cast<int64_t*>(ptr);
-        ptr += 8 * tcols * nkw;
-        S.wpos = reinterpret_cast<unsigned long long*>(ptr);
-        ptr += 8 * tcols * ((nk + 1) / 2);
-        S.queue = reinterpret_cast<uint2*>(ptr);
-        ptr += 8 * nw * kQueue;
+        ptr += 16 * WD;
+        S.ring = reinterpret_cast<uint2*>(ptr);
+        ptr += 8 * RING;
+        S.cur = reinterpret_cast<uint32_t*>(ptr);
+        ptr += 4 * p.cap;
         S.mask = reinterpret_cast<uint32_t*>(ptr);
-        ptr += 4 * tcols * nkw;
-        S.nearb = reinterpret_cast<uint32_t*>(ptr);
-        ptr += 4 * tcols * nkw;
-        S.lpre = reinterpret_cast<int32_t*>(ptr);
-        ptr += 4 * tcols * nkw;
-        S.sortbuf = reinterpret_cast<int32_t*>(ptr);
-        ptr += 4 * nw * kSortCap;
-        S.active = reinterpret_cast<int32_t*>(ptr);
-        ptr += 4 * tile_d;
-        if (BAND) {
-            S.sx = reinterpret_cast<float*>(ptr);
-            S.sy = S.sx + nthr;
-            S.sband = reinterpret_cast<int*>(S.sy + nthr);
-            S.slist = reinterpret_cast<uint16_t*>(S.sband + nthr);
-        } else {
-            S.sx = S.sy = nullptr;
-            S.sband = nullptr;
-            S.slist = nullptr;
-        }
+        S.nearb = S.mask + ncols * nkw;
+        S.lpre = reinterpret_cast<int32_t*>(S.nearb + ncols * nkw);
     }
-    __shared__ int s_cnt[kBuckets];
-    S.cnt = s_cnt;
-    __shared__ int s_nactive;
-    uint2* q = S.queue + warp * kQueue;
-    __shared__ int64_t sh[33];
     const int tiles_phi = (p.K.nphi + SPHI - 1) / SPHI;
-    const int tiles_d = (p.K.nd + tile_d - 1) / tile_d;
-    const int64_t items = (int64_t)p.n_events * tiles_phi * tiles_d;
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int e = (int)(item / ((int64_t)tiles_phi * tiles_d));
-        const int t = (int)(item - (int64_t)e * tiles_phi * tiles_d);
-        const int tp = t / tiles_d, td = t - (t / tiles_d) * tiles_d;
-        const int i0 = tp * SPHI, j0 = td * tile_d;
-        const int nj = min(tile_d, p.K.nd - j0);
+    const int tiles_d = (p.K.nd + WD - 1) / WD;
+    const int64_t tiles = (int64_t)tiles_phi * tiles_d;
+    const int64_t n_items = (int64_t)p.n_events * tiles;
+    const unsigned nku = (unsigned)nk;
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    const unsigned lt = lanemask_lt();
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(p.queue, 1ull);
+        const int64_t item = (int64_t)__shfl_sync(0xffffffffu, it, 0);
+        if (item >= n_items) break;
+        const int el = (int)(item / tiles);
+        const int64_t t = item - (int64_t)el * tiles;
+        const int e = p.order ? p.order[el] : el;
+        const int tp = (int)(t / tiles_d), td = (int)(t - (int64_t)tp * tiles_d);
+        const int i0 = tp * SPHI, j0 = td * WD;
+        const int nj = min(WD, p.K.nd - j0);
         const int nrows = min(SPHI, p.K.nphi - i0);
-        // tile columns c = j * SPHI + r; first-peak ids and local slots
-        int64_t carry = 0;
-        bool any = false;
-        __syncthreads();
-        for (int c0 = 0; c0 < tcols; c0 += nthr) {
-            const int c = c0 + tid;
-            const int j = c / SPHI, r = c - (c / SPHI) * SPHI;
-            const bool live = c < tcols && j < nj && r < nrows;
-            const int64_t col = live ? ((int64_t)e * p.K.nphi + i0 + r) * p.K.nd + j0 + j : 0;
-            const int n = live ? p.npk[col] : 0;
-            int64_t tot;
-            const int64_t ex = block_exscan64(n, sh, &tot);
-            if (c < tcols) {
-                const int64_t cb = live ? p.colbase[col] : 0;
-                for (int w = 0; w < nkw; ++w) {
-                    const uint32_t m = live ? p.mask[col * nkw + w] : 0u;
-                    const int wp = live ? p.wpre[col * nkw + w] : 0;
-                    S.mask[c * nkw + w] = m;
-                    S.lpre[c * nkw + w] = (int)(carry + ex) + wp;
-                    S.gpre[c * nkw + w] = cb + wp;
-                }
-                any |= n > 0 && cb < p.peak_cap;
-            }
-            carry += tot;
-        }
-        if (!__syncthreads_or(any)) continue;
-        for (int j = tid; j < nj; j += nthr) S.dt[j] = p.dtab[j0 + j];
-        // compacted list of the d0 columns that hold a peak in any of the tile's rows
-        if (warp == 0) {
-            int na = 0;
-            for (int jb = 0; jb < nj; jb += 32) {
-                const int j = jb + lane;
-                bool act = false;
-                if (j < nj)
-                    for (int r = 0; r < SPHI; ++r)
-                        for (int w = 0; w < nkw; ++w) act |= S.mask[(j * SPHI + r) * nkw + w] != 0u;
-                const unsigned b = __ballot_sync(0xffffffffu, act);
-                if (act) S.active[na + __popc(b & lanemask_lt())] = j;
-                na += __popc(b);
-            }
-            if (lane == 0) s_nactive = na;
-        }
-        // near bits (a peak within `window`) and each peak's first CSR position
-        for (int v = tid; v < tcols * nkw; v += nthr) {
+        const int nvalid = nrows * nj;  // columns c = r * WD + j, consecutive in the column numbering
+        const int64_t colA = ((int64_t)e * p.K.nphi + i0) * p.K.nd + j0;
+        const bool live = lane < nvalid;
+        const int n = live ? p.npk[colA + lane] : 0;
+        const int64_t cb = live ? p.colbase[colA + lane] : 0;
+        const int64_t P0 = __shfl_sync(0xffffffffu, cb, 0);
+        const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)n);
+        // peaks of the item that are stored (id < peak_cap)
+        const int npk = (int)clamp64(p.peak_cap - P0, 0, tot);
+        if (npk == 0) continue;
+        const int lo_c = (int)(cb - P0), hi_c = lo_c + n;  // this lane's column: local ids [lo_c, hi_c)
+        __syncwarp();  // the previous item's tables are no longer read
+        for (int v = lane; v < ncols * nkw; v += 32) {
             const int c = v / nkw, w = v - (v / nkw) * nkw;
-            const uint32_t* m = S.mask + c * nkw;
+            const bool ok = c < nvalid;
+            const int64_t col = colA + c;
+            S.mask[v] = ok ? p.mask[col * nkw + w] : 0u;
+            S.lpre[v] = ok ? (int)(p.colbase[col] - P0) + p.wpre[col * nkw + w] : 0;
+        }
+        if (lane < nj) S.dt[lane] = p.dtab[j0 + lane];
+        __syncwarp();
+        for (int v = lane; v < ncols * nkw; v += 32) {
+            const int w = v - (v / nkw) * nkw;
+            const uint32_t* m = S.mask + (v - w);
             uint32_t nb = m[w];
-            for (int o = 1; o <= p.window; ++o) {
-                const uint32_t hi_w = w + 1 < nkw ? m[w + 1] : 0u, lo_w = w > 0 ? m[w - 1] : 0u;
+            const uint32_t hi_w = w + 1 < nkw ? m[w + 1] : 0u, lo_w = w > 0 ? m[w - 1] : 0u;
+            for (int o = 1; o <= p.window; ++o)
                 nb |= (m[w] >> o) | (hi_w << (32 - o)) | (m[w] << o) | (lo_w >> (32 - o));
-            }
             S.nearb[v] = nb;
-            uint32_t bits = m[w];
-            int below = 0;
-            while (bits) {
-                bits &= bits - 1;
-                const int64_t pid = S.gpre[v] + below;
-                S.wpos[S.lpre[v] + below] =
-                    pid < p.peak_cap ? (unsigned long long)p.peak_offsets[pid] : ~0ull >> 1;
-                ++below;
-            }
         }
         float cp[SPHI], sp[SPHI];
 #pragma unroll
@@ -1111,43 +915,121 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p, cons
         }
         const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
         const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
-        int qn = 0;
-        __syncthreads();
-        const int na = s_nactive;
-        if (BAND && na > 0) {
-            // the active columns span [S.active[0], S.active[na-1]]: bands are clipped to it
-            const int ja = j0 + S.active[0], jb = j0 + S.active[na - 1];
-            assoc_band_hits<SPHI, NK>(p, S, q, qn, cp, sp, ja, jb - ja + 1, j0, nrows, nk, nkw, hb, he, lane);
-        } else {
-            const int64_t nfull = ((he - hb) / nthr) * nthr;
-            for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
-                assoc_one_hit<SPHI, NK, false>(p, S, q, qn, cp, sp, na, nk, nkw, h, true, lane);
-            {
-                const int64_t h = hb + nfull + tid;
-                if (hb + nfull + (tid - lane) < he)
-                    assoc_one_hit<SPHI, NK, true>(p, S, q, qn, cp, sp, na, nk, nkw, h, h < he, lane);
-            }
-        }
-        queue_drain(p, S, q, qn, nkw, nk, lane);
-        __syncthreads();
-        // ascending hit order within every complete row of the tile's peaks
-        int32_t* buf = S.sortbuf + warp * kSortCap;
-        for (int c = warp; c < tcols; c += nw) {
-            for (int w = 0; w < nkw; ++w) {
-                uint32_t m = S.mask[c * nkw + w];
-                int below = 0;
-                while (m) {
-                    m &= m - 1;
-                    const int64_t pid = S.gpre[c * nkw + w] + below;
-                    const int local = S.lpre[c * nkw + w] + below;
-                    ++below;
-                    if (pid >= p.peak_cap) continue;
-                    const int64_t off = p.peak_offsets[pid];
-                    const int64_t end = (int64_t)S.wpos[local];
-                    if (end > p.pair_cap) continue;  // row cut by the output cap
-                    sort_row(p.hit_idx + off, (int)(end - off), buf, lane);
+        // a pass's rows span at most cap * (event hits) pairs: keep that below 2^32
+        const int64_t eh = he - hb > 1 ? he - hb : 1;
+        const int step = (int)clamp64(0xFFFFFFFFll / eh, 1, p.cap);
+        const float dlo = S.dt[0].x, dhi = S.dt[nj - 1].x;
+        for (int L0 = 0; L0 < npk; L0 += step) {
+            AssocPass ps;
+            ps.L0 = L0;
+            ps.L1 = min(npk, L0 + step);
+            ps.whole = L0 == 0 && ps.L1 == tot;
+            ps.Q = p.peak_offsets[P0 + L0];
+            __syncwarp();
+            for (int l = lane; l < ps.L1 - L0; l += 32)
+                S.cur[l] = (uint32_t)(p.peak_offsets[P0 + L0 + l] - ps.Q);
+            // columns holding a peak of this pass, and the d0 columns among them
+            const unsigned cmask = __ballot_sync(0xffffffffu, live && hi_c > ps.L0 && lo_c < ps.L1);
+            unsigned jmask = 0;
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) jmask |= (unsigned)((unsigned long long)cmask >> (r * WD));
+            jmask &= (unsigned)((1ull << nj) - 1ull);
+            unsigned head = 0, tail = 0;
+            __syncwarp();
+            int64_t hh = hb + lane;
+            float xn = hh < he ? p.x[hh] : 0.0f;
+            float yn = hh < he ? p.y[hh] : 0.0f;
+            for (int64_t h0 = hb; h0 < he; h0 += 32, hh += 32) {
+                const bool valid = hh < he;
+                const float x = xn, y = yn;
+                if (hh + 32 < he) {  // next chunk's coordinates
+                    xn = p.x[hh + 32];
+                    yn = p.y[hh + 32];
+                }
+                const HitFast hf = hit_fast(x, y, p.K);
+                float q_[SPHI], qs[SPHI];
+#pragma unroll
+                for (int r = 0; r < SPHI; ++r) {
+                    q_[r] = q_of(x, y, cp[r], sp[r]);
+                    qs[r] = q_[r] * S2;
+                }
+                unsigned jm = jmask;
+                if (BAND) {
+                    // union of the lanes' d0 bands: columns outside it cannot vote
+                    unsigned bm = 0;
+#pragma unroll
+                    for (int r = 0; r < SPHI; ++r) {
+                        int jlo, jhi;
+                        d0_band(hf.r2, q_[r], dlo, dhi, j0, nj, p.K, jlo, jhi);
+                        if (valid && jhi >= jlo)
+                            bm |= (unsigned)(((2ull << (jhi - j0)) - 1ull) & ~((1ull << (jlo - j0)) - 1ull));
+                    }
+                    jm &= __reduce_or_sync(0xffffffffu, bm);
+                }
+                // U columns per step, SPHI rows each: independent cells for the
+                // pipelines; steps past the last active column repeat column
+                // jj[0] with its cells masked off
+                while (jm) {
+                    int jj[U];
+                    bool jv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        jv[u] = jm != 0u;
+                        jj[u] = jv[u] ? __ffs(jm) - 1 : jj[0];
+                        jm &= jm - 1u;
+                    }
+                    int kb[U][SPHI];
+                    bool und_any = false;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float4 dt = S.dt[jj[u]];
+                        const float Rj = hf.r2 + dt.z;
+#pragma unroll
+                        for (int r = 0; r < SPHI; ++r) {
+                            const int c = r * WD + jj[u];
+                            const bool on = valid && jv[u] && (SPHI == 1 || ((cmask >> c) & 1u));
+                            const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+                            kb[u][r] = ((o.flo == o.fhi) & (o.kb < nku) & on) ? (int)o.kb : -1;
+                            und_any |= (o.flo != o.fhi) & on;
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, und_any)) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const float4 dt = S.dt[jj[u]];
+                            const float Rj = hf.r2 + dt.z;
+#pragma unroll
+                            for (int r = 0; r < SPHI; ++r) {
+                                const int c = r * WD + jj[u];
+                                const bool on = valid && jv[u] && (SPHI == 1 || ((cmask >> c) & 1u));
+                                const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+                                if ((o.flo != o.fhi) && on && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi))
+                                    kb[u][r] = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+#pragma unroll
+                        for (int r = 0; r < SPHI; ++r) {
+                            const int c = r * WD + jj[u];
+                            const int b = kb[u][r];
+                            const uint32_t nb = S.nearb[c * nkw + (b >= 0 ? (b >> 5) : 0)];
+                            const bool cand = b >= 0 && ((nb >> (b & 31)) & 1u);
+                            const unsigned m = __ballot_sync(0xffffffffu, cand);
+                            if (cand)
+                                S.ring[(tail + __popc(m & lt)) & (RING - 1)] =
+                                    make_uint2(((unsigned)c << 16) | (unsigned)b, (unsigned)hh);
+                            tail += __popc(m);
+                        }
+                    }
+                    while (tail - head >= 32) {
+                        assoc_drain<RING>(p, S, nkw, nk, head, 32, ps, lane);
+                        head += 32;
+                    }
                 }
             }
+            if (tail != head) assoc_drain<RING>(p, S, nkw, nk, head, (int)(tail - head), ps, lane);
         }
     }
 }
@@ -1363,26 +1245,22 @@ static void* assoc_instance(int tile_phi, int nk, bool band) {
     return nullptr;
 }
 
-size_t assoc_smem(int tile_phi, int tile_d, int nk, int threads, bool band) {
-    return assoc_smem_bytes(tile_phi, tile_d, nk, threads, band);
-}
+size_t assoc_warp_smem(int rows, int wd, int nk, int cap) { return assoc_warp_bytes(rows, wd, nk, cap); }
 
-cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band) {
+cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band, int threads, int* blocks_per_sm) {
     void* f = assoc_instance(tile_phi, nk, band);
     if (!f) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
 
-cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int tile_d, int threads, cudaStream_t s) {
+cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int grid, cudaStream_t s) {
     if ((int64_t)p.n_events * p.K.nphi == 0) return cudaSuccess;
     void* f = assoc_instance(tile_phi, p.K.nk, p.band != 0);
     if (!f) return cudaErrorInvalidValue;
-    const int tiles = ((p.K.nphi + tile_phi - 1) / tile_phi) * ((p.K.nd + tile_d - 1) / tile_d);
-    const int64_t items = (int64_t)p.n_events * tiles;
-    const int grid = (int)std::min<int64_t>(items, 152 * 32);
-    const int smem = (int)assoc_smem_bytes(tile_phi, tile_d, p.K.nk, threads, p.band != 0);
-    int td = tile_d;
-    void* args[] = {const_cast<AssocParams*>(&p), &td};
+    const int smem = (int)(p.warp_bytes * (threads / 32));
+    void* args[] = {const_cast<AssocParams*>(&p)};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
 }
 

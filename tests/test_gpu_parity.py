@@ -295,12 +295,9 @@ def test_overflow_and_budget(ht):
     assert cnt[0] == len(full[0]) and cnt[1] == len(full[2])
     pk, po, hi = res.host()
     assert np.array_equal(pk, full[0][:10])
-    # rows that end below the pair cap are exact; the crossing row is a subset
+    # rows that end below the pair cap are exact; the crossing row holds its first hits
     po_full, hi_full = full[1], full[2]
-    cross = int(np.searchsorted(po_full, 100, side="right")) - 1
-    a = int(po_full[cross])
-    assert np.array_equal(hi[:a], hi_full[:a])
-    assert set(hi[a:100].tolist()) <= set(hi_full[a:po_full[cross + 1]].tolist())
+    assert np.array_equal(hi[:100], hi_full[:100])
     ctx.set_option(ht.HT_OPT_ACC_BUDGET, g.n_phi * g.n_d0 * g.n_kappa * 4 * 2)
     with pytest.raises(ht.HtError) as ei:
         ctx.vote(ht.Hits.from_batch(b, device="cuda"))
@@ -427,6 +424,40 @@ def test_peaks_with_few_phi_rows(ht, oracle_mod, n_phi):
         assert np.array_equal(po, po_o) and np.array_equal(hi, hi_o)
 
 
+def test_association_windows(ht, oracle_mod):
+    """Windows 0, 2, 3 and 6 at a low threshold: hits whose window holds two
+    or more peaks of a column, ranked over one to four rounds of peaks."""
+    w = synth.WORKLOADS["dense_event_500trk"]
+    b = synth.generate(w, n_events=1)
+    g = synth.Grid(48, 12, 64, -25.0, 25.0, -0.0114, 0.0114)
+    acc_o = oracle_mod.vote(g, b.x, b.y, b.event_offsets)
+    pk_o = oracle_mod.peaks(g, acc_o, 3)
+    for window in (0, 2, 3, 6):
+        pk, po, hi = _run(ht, g, b, 3, window)
+        assert np.array_equal(pk, pk_o)
+        po_o, hi_o = oracle_mod.associate(g, b.x, b.y, b.event_offsets, pk_o, window)
+        assert np.array_equal(po, po_o) and np.array_equal(hi, hi_o), window
+
+
+def test_association_passes(ht, oracle_mod):
+    """Threshold 1 on a 512-bin kappa axis: a row's 32-column block holds more
+    peaks than the 512 row cursors a warp keeps for this grid, so the block
+    is walked in several passes."""
+    w = synth.WORKLOADS["dense_event_500trk"]
+    b = synth.generate(w, n_events=1)
+    g = synth.Grid(16, 32, 512, -25.0, 25.0, -0.0114, 0.0114)
+    acc_o = oracle_mod.vote(g, b.x, b.y, b.event_offsets)
+    pk_o = oracle_mod.peaks(g, acc_o, 1)
+    per_row = np.bincount(pk_o["i_phi"], minlength=g.n_phi)
+    assert per_row.max() > 512
+    pk, po, hi = _run(ht, g, b, 1, 1, pair_cap=1 << 28)
+    assert np.array_equal(pk, pk_o)
+    win = np.array([acc_o[0, p["i_phi"], p["i_d0"], max(p["i_kappa"] - 1, 0):p["i_kappa"] + 2].sum()
+                    for p in pk_o], np.int64)
+    assert np.array_equal(np.diff(po), win)
+    _check_csr_rows(oracle_mod, g, b, pk, po, hi, 1, 1500)
+
+
 def test_overflow_across_waves(ht):
     """Caps hit in the first wave: later waves lie wholly past the caps; the
     stored prefix and the true counts must match an unbounded run."""
@@ -449,5 +480,8 @@ def test_overflow_across_waves(ht):
         assert np.array_equal(pk, full[0][:pc])
         n_ok = int(np.searchsorted(po, qc, side="right")) - 1   # rows ending at or below the cap
         assert np.array_equal(po[: n_ok + 1], full[1][: n_ok + 1])
-        assert np.array_equal(hi[: po[n_ok]], full[2][: po[n_ok]])
+        # every slot below the cap that belongs to a stored peak's row, the
+        # crossing row's first hits included
+        m = min(qc, int(full[1][len(pk)]))
+        assert np.array_equal(hi[:m], full[2][:m])
         ctx.close()
