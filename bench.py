@@ -194,7 +194,7 @@ def run_gpu(args):
         # accumulator memory admitted for this many events at a time (waves)
         ctx.set_option(ht.HT_OPT_ACC_BUDGET, args.waves_of * 4 * g.n_phi * g.n_d0 * g.n_kappa)
     hits_d = ht.Hits.from_batch(batch, device=dev)
-    if args.prune:
+    if args.prune is not None:
         ctx.set_option(ht.HT_OPT_PRUNE, args.prune)
     if args.tile:
         for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
@@ -389,7 +389,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--prune", type=int, default=0, help="HT_OPT_PRUNE bits (1 vote, 2 association)")
+    ap.add_argument("--prune", type=int, default=None,
+                    help="HT_OPT_PRUNE bits (1 vote, 2 association); default: the library's (3)")
     ap.add_argument("--workload", default=WORKLOAD, help="workload name (secondary lines use --no-extras)")
     ap.add_argument("--waves-of", type=int, default=0, help="admit accumulators for this many events at a time")
     ap.add_argument("--events", type=int, default=None, help="events per batch (default: the full 4096)")

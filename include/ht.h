@@ -129,9 +129,12 @@ typedef struct {
                                       more than 1 only with HT_OPT_ATILE_D0 = n_d0 */
 #define HT_OPT_ATILE_D0 11         /* d0 columns per association item (0 = auto); rows x
                                       columns of an item at most 32 */
-#define HT_OPT_PRUNE 12            /* bit 0: the vote, bit 1: the association walk only each (hit,
-                                      phi0) row's d0 band that can hold a vote (a proven superset)
-                                      instead of every cell; same results.  Default 0. */
+#define HT_OPT_PRUNE 12            /* bit 0: the vote, bit 1: the association first drop the hits
+                                      whose d0 band (a proven superset of the columns where a hit
+                                      can vote) misses the tile's rows, then evaluate the remaining
+                                      hits over the hull (vote) or union (association) of their
+                                      bands; same results.  Default 3; no effect when the kappa
+                                      range does not contain 0. */
 
 #define HT_MODE_BATCHED 0 /* one persistent launch per kernel over all (event, tile) items */
 #define HT_MODE_PLAIN 1   /* one launch sequence per event */

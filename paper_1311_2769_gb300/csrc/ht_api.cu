@@ -75,7 +75,7 @@ struct ht_ctx {
     int mode = HT_MODE_BATCHED;
     int tile_phi = 0, tile_d = 0, threads = 0;
     int atile_phi = 0, atile_d = 0;  // association item (0 = auto)
-    int prune = 0;                   // bit 0: vote, bit 1: association evaluate only d0 bands
+    int prune = 3;                   // bit 0: vote, bit 1: association drop hits without a d0 band
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
@@ -220,11 +220,15 @@ KConsts make_consts(const ht_grid& g, const std::vector<float>& d0) {
     K.cGb1 = (float)(64.0 * u * u * V2);
     K.cGb2 = (float)(20.0 * u * u * S2);
     K.cDb = (float)std::ldexp(1.0, -23);
-    // d0 bands (pruned vote): kappa window widened by two bins
+    // d0 bands (pruned vote and association): kappa window widened by two
+    // bins.  The band's u bounds carry relative errors of a few ulps (|u| <=
+    // 1.5e4 + |d0| for hits within the validated 1e4 box), so a column must
+    // be wide enough for the one-column margin to absorb them.
     {
         const double kmn = (double)g.kappa_min, kmx = (double)g.kappa_max, dk = (kmx - kmn) / nk;
         const double A = kmn - 2.0 * dk, B = kmx + 2.0 * dk;
-        K.band_ok = (A < 0.0 && B > 0.0) ? 1 : 0;
+        const double colw = ((double)g.d0_max - (double)g.d0_min) / g.n_d0;
+        K.band_ok = (A < 0.0 && B > 0.0 && colw >= 1e-5 * (2e4 + (double)K.dabs)) ? 1 : 0;
         K.bA2 = (float)(A * A);
         K.bB2 = (float)(B * B);
         K.biA = (float)(1.0 / std::fabs(A));

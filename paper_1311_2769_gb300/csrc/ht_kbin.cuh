@@ -46,9 +46,15 @@ struct KConsts {
     // stage 3 (binary64 definition)
     double kmin, scale;
     // d0 band of a (hit, phi row): kappa window widened by two bins each side
-    int band_ok;           // 0: kappa range does not straddle 0, bands are the full tile
+    int band_ok;           // 0: kappa range does not straddle 0 or d0 columns too narrow: no bands
     float bA2, bB2, biA, biB, bdfirst, bidd;
 };
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // The d0 columns [jlo, jhi] of the tile [j0, j0 + nj) where hit (x, y) can vote
 // in the row with table values (c, s), as a superset: with u = d0 - q and
@@ -64,11 +70,15 @@ __device__ __forceinline__ void d0_band(float r2, float q, float dlo, float dhi,
     const float p2 = fmaxf(fmaf(-q, q, r2), 0.0f);
     const float DA = fmaf(-K.bA2, p2, 1.0f);
     const float DB = fmaf(-K.bB2, p2, 1.0f);
-    const float sA = sqrtf(fmaxf(DA, 0.0f));
-    const float sB = sqrtf(fmaxf(DB, 0.0f));
-    const float a1 = DA > 0.0f ? ((K.bA2 * p2) * K.biA) / (1.0f + sA) : BIG;
+    // approximate square roots and reciprocals (relative errors of a few
+    // ulps): a root off by eps moves kappa by |dkappa/du| eps, far below the
+    // two bins the window is widened by, and the u bounds stay well inside
+    // the one-column margin (the host keeps bands off for narrower columns)
+    const float sA = DA > 0.0f ? DA * rsqrtf(DA) : 0.0f;
+    const float sB = DB > 0.0f ? DB * rsqrtf(DB) : 0.0f;
+    const float a1 = DA > 0.0f ? ((K.bA2 * p2) * K.biA) * rcp_approx(1.0f + sA) : BIG;
     const float a2 = DA > 0.0f ? (1.0f + sA) * K.biA : BIG;
-    const float b2 = DB > 0.0f ? ((-(K.bB2 * p2)) * K.biB) / (1.0f + sB) : -BIG;
+    const float b2 = DB > 0.0f ? ((-(K.bB2 * p2)) * K.biB) * rcp_approx(1.0f + sB) : -BIG;
     const float b1 = DB > 0.0f ? (-(1.0f + sB)) * K.biB : -BIG;
     const float ulo = dlo - q, uhi = dhi - q;
     const float lo = ulo < b1 ? ulo
@@ -84,12 +94,6 @@ __device__ __forceinline__ void d0_band(float r2, float q, float dlo, float dhi,
     const float jh = floorf(((hi + q) - K.bdfirst) * K.bidd) + 2.0f;
     jlo = (int)fminf(fmaxf(jl, (float)j0), (float)(j0 + nj));
     jhi = (int)fminf(fmaxf(jh, (float)(j0 - 1)), (float)(j0 + nj - 1));
-}
-
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
 }
 
 // ---- stage 1 -------------------------------------------------------------

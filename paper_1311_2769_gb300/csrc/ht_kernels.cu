@@ -63,12 +63,13 @@ struct TileHit {
     HitFast hf;
 };
 
-// One hit against every column of the tile.  TAIL: lanes past the event's
-// last hit stay in the loop (the full-mask vote needs all 32) but are masked.
+// One hit against the tile's columns ja..jb (warp-uniform).  TAIL: lanes
+// without a hit stay in the loop (the full-mask vote needs all 32) but are
+// masked.
 template <int SPHI, int NK, bool TAIL>
 __device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* cp, const float* sp,
-                                             const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int nj, int nk,
-                                             int64_t h, bool valid) {
+                                             const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
+                                             int nk, int64_t h, bool valid) {
     const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
     const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
     const HitFast hf = hit_fast(x, y, p.K);
@@ -81,8 +82,8 @@ __device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* c
     }
     const unsigned nku = (unsigned)nk;
     const int col_words = SPHI * nk;
-    uint32_t col_sh = acc_sh;
-    for (int j = 0; j < nj; ++j, col_sh += 4u * col_words) {
+    uint32_t col_sh = acc_sh + 4u * (unsigned)(ja * col_words);
+    for (int j = ja; j <= jb; ++j, col_sh += 4u * col_words) {
         const float4 dt = dt_s[j];
         const float Rj = hf.r2 + dt.z;
         bool und = false;
@@ -164,11 +165,11 @@ __global__ void __launch_bounds__(256, 3) vote_kernel(const VoteParams p) {
 
         const int64_t nfull = ((he - hb) / nthr) * nthr;
         for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
-            vote_one_hit<SPHI, NK, false>(p, cp, sp, dt_s, acc_s, acc_sh, nj, nk, h, true);
+            vote_one_hit<SPHI, NK, false>(p, cp, sp, dt_s, acc_s, acc_sh, 0, nj - 1, nk, h, true);
         {
             const int64_t h = hb + nfull + tid;
             if (hb + nfull + (tid - lane) < he)  // warps with at least one hit left
-                vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, nj, nk, h, h < he);
+                vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, 0, nj - 1, nk, h, h < he);
         }
         __syncthreads();
 
@@ -193,39 +194,46 @@ __global__ void __launch_bounds__(256, 3) vote_kernel(const VoteParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// pruned vote: only the d0 band of each (hit, phi row) is evaluated
+// pruned vote: hits without a band in the tile are dropped first
 // ---------------------------------------------------------------------------
-// Per chunk of blockDim hits: every thread computes its hit's band over the
-// tile's rows (the union of the rows' d0_band) and files the hit into one of
-// four buckets by band length (<= nj/8, nj/4, nj/2, nj).  Warps then take 32
-// hits of one bucket at a time; each lane walks its own band from its own
-// first column, the warp for as many steps as the longest band among its 32
-// lanes, so lanes of a warp do similar amounts of work.  Cells outside every
-// band cannot vote (they are out of the kappa range in binary64), so the
-// accumulator is the same as the full vote's.
-constexpr int kBuckets = 4;
+// Each warp takes its hits 32 at a time and computes, per hit, the union of
+// the tile rows' d0 bands (d0_band: a proven superset of the columns where
+// the hit can vote).  Hits with an empty union are dropped; the others enter
+// a per-warp queue, and every 32 queued hits run the ordinary cell loop over
+// the hull of their 32 bands.  Cells outside a hit's band cannot vote (they
+// are out of the kappa range in binary64), so the accumulator is the full
+// vote's.  On the batch workload about two thirds of the (hit, tile) pairs
+// of a 4 x 16 tile have an empty band.
+constexpr int kHitQueue = 64;  // per-warp queue of banded hits (run 32 at a time)
+
+template <int SPHI, int NK>
+__device__ __forceinline__ void vote_queued(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
+                                            uint32_t* acc_s, uint32_t acc_sh, const uint2* hq, unsigned head, int n,
+                                            int nj, int nk, int lane) {
+    __syncwarp();
+    const bool valid = lane < n;
+    const uint2 ent = valid ? hq[(head + lane) & (kHitQueue - 1)] : make_uint2(0u, 0u);
+    const int lo = valid ? (int)(ent.y & 0xFFFFu) : nj, hi = valid ? (int)(ent.y >> 16) : -1;
+    const int ja = __reduce_min_sync(0xffffffffu, lo), jb = __reduce_max_sync(0xffffffffu, hi);
+    __syncwarp();  // entries read before their slots are reused
+    vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid);
+}
 
 template <int SPHI, int NK>
 __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* dt_s = reinterpret_cast<float4*>(smem_raw);
     const int nthr = blockDim.x;
-    // chunk records follow the d0 table; the accumulator tile follows them
-    float* sx = reinterpret_cast<float*>(smem_raw + 16 * p.tile_d);
-    float* sy = sx + nthr;
-    int* sband = reinterpret_cast<int*>(sy + nthr);           // jlo | (len << 16)
-    uint16_t* slist = reinterpret_cast<uint16_t*>(sband + nthr);  // [kBuckets][nthr]
-    uint32_t* acc_s = reinterpret_cast<uint32_t*>(slist + kBuckets * nthr + (nthr & 1 ? 2 : 0));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    uint2* hq = reinterpret_cast<uint2*>(smem_raw + 16 * p.tile_d) + warp * kHitQueue;
+    uint32_t* acc_s = reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d + 8 * kHitQueue * nw);
     __shared__ int s_item;
-    __shared__ int s_cnt[kBuckets];
 
     const int nk = NK ? NK : p.K.nk;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
     const int tiles = p.tiles_phi * p.tiles_d;
     const int col_words = SPHI * nk;
     const uint32_t acc_sh = smem_addr(acc_s);
-    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
-    const unsigned nku = (unsigned)nk;
+    const unsigned lt = lanemask_lt();
 
     for (int it = 0;; ++it) {
         int item;
@@ -259,109 +267,38 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
             cp[r] = p.cphi[i];
             sp[r] = p.sphi[i];
         }
-        const float dlo = p.dtab[j0].x, dhi = p.dtab[j0 + nj - 1].x;
-        int lim[kBuckets];
-        lim[0] = max(1, nj / 8);
-        lim[1] = max(1, nj / 4);
-        lim[2] = max(1, nj / 2);
-        lim[3] = nj;
         if (p.stats && tid == 0) atomicAdd(&p.stats[0], (unsigned long long)((he - hb) * nrows * nj));
+        __syncthreads();
 
-        for (int64_t cb = hb; cb < he; cb += nthr) {
-            if (tid < kBuckets) s_cnt[tid] = 0;
-            __syncthreads();
-            // phase 1: band of this thread's hit over the tile's rows, filed by length
-            const int64_t h = cb + tid;
-            int jlo = j0 + nj, jhi = j0 - 1;
-            float x = 0.0f, y = 0.0f;
-            if (h < he) {
-                x = p.x[h];
-                y = p.y[h];
-                if (p.K.band_ok) {
-                    const float r2 = fmaf(x, x, __fmul_rn(y, y));
+        const float dlo = dt_s[0].x, dhi = dt_s[nj - 1].x;
+        unsigned head = 0, tail = 0;
+        for (int64_t c0 = hb + warp * 32; c0 < he; c0 += nthr) {
+            const int64_t h = c0 + lane;
+            const bool valid = h < he;
+            const float x = valid ? p.x[h] : 0.0f;
+            const float y = valid ? p.y[h] : 0.0f;
+            const float r2 = fmaf(x, x, __fmul_rn(y, y));
+            int lo = nj, hi = -1;
 #pragma unroll
-                    for (int r = 0; r < SPHI; ++r) {
-                        if (r >= nrows) break;
-                        int a, b;
-                        d0_band(r2, q_of(x, y, cp[r], sp[r]), dlo, dhi, j0, nj, p.K, a, b);
-                        if (b >= a) {
-                            jlo = min(jlo, a);
-                            jhi = max(jhi, b);
-                        }
-                    }
-                } else {
-                    jlo = j0;
-                    jhi = j0 + nj - 1;
+            for (int r = 0; r < SPHI; ++r) {
+                int jl, jh;
+                d0_band(r2, q_of(x, y, cp[r], sp[r]), dlo, dhi, j0, nj, p.K, jl, jh);
+                if (jh >= jl) {
+                    lo = min(lo, jl - j0);
+                    hi = max(hi, jh - j0);
                 }
             }
-            const int len = jhi >= jlo ? jhi - jlo + 1 : 0;
-            sx[tid] = x;
-            sy[tid] = y;
-            sband[tid] = (jlo - j0) | (len << 16);
-#pragma unroll
-            for (int bk = 0; bk < kBuckets; ++bk) {
-                const bool in = len > 0 && len <= lim[bk] && (bk == 0 || len > lim[bk - 1]);
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                int base = 0;
-                if (lane == 0 && m) base = atomicAdd(&s_cnt[bk], __popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (in) slist[bk * nthr + base + __popc(m & lanemask_lt())] = (uint16_t)tid;
+            const bool keep = valid && hi >= lo;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) hq[(tail + __popc(m & lt)) & (kHitQueue - 1)] = make_uint2((unsigned)h, (unsigned)lo | ((unsigned)hi << 16));
+            tail += __popc(m);
+            if (tail - head >= 32) {
+                vote_queued<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, 32, nj, nk, lane);
+                head += 32;
             }
-            __syncthreads();
-            // phase 2: warps take 32 hits of one bucket at a time
-            int groups = 0;
-            int gstart[kBuckets + 1];
-#pragma unroll
-            for (int bk = 0; bk < kBuckets; ++bk) {
-                gstart[bk] = groups;
-                groups += (s_cnt[bk] + 31) >> 5;
-            }
-            gstart[kBuckets] = groups;
-            for (int g = warp; g < groups; g += nw) {
-                int bk = 0;
-#pragma unroll
-                for (int b2 = 1; b2 < kBuckets; ++b2) bk += g >= gstart[b2];
-                const int idx = (g - gstart[bk]) * 32 + lane;
-                const bool has = idx < s_cnt[bk];
-                const int ht = has ? slist[bk * nthr + idx] : 0;
-                const int bd = has ? sband[ht] : 0;
-                const int jl = bd & 0xFFFF, ln = bd >> 16;
-                const float hx = sx[ht], hy = sy[ht];
-                const HitFast hf = hit_fast(hx, hy, p.K);
-                float q[SPHI], qs[SPHI];
-#pragma unroll
-                for (int r = 0; r < SPHI; ++r) {
-                    q[r] = q_of(hx, hy, cp[r], sp[r]);
-                    qs[r] = q[r] * S2;
-                }
-                const int steps = __reduce_max_sync(0xffffffffu, ln);
-                for (int s = 0; s < steps; ++s) {
-                    const bool live = s < ln;
-                    const int j = live ? jl + s : 0;
-                    const float4 dt = dt_s[j];
-                    const float Rj = hf.r2 + dt.z;
-                    const uint32_t col_sh = acc_sh + 4u * (unsigned)(j * col_words);
-                    bool und = false;
-#pragma unroll
-                    for (int r = 0; r < SPHI; ++r) {
-                        const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
-                        red_if_vote(col_sh + 4u * ((unsigned)(r * nk) + o.kb), o.flo, o.fhi, o.kb, nku, live);
-                        und |= (o.flo != o.fhi) & live;
-                    }
-                    if (__any_sync(0xffffffffu, und)) {
-#pragma unroll
-                        for (int r = 0; r < SPHI; ++r) {
-                            const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
-                            if ((o.flo != o.fhi) && live && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi)) {
-                                const int kk = cell_slow(hx, hy, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
-                                if (kk >= 0) atomicAdd(acc_s + j * col_words + r * nk + kk, 1u);
-                            }
-                        }
-                    }
-                }
-            }
-            __syncthreads();
         }
+        if (tail != head) vote_queued<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, (int)(tail - head), nj, nk, lane);
+        __syncthreads();
 
         uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
         const int nrj = nrows * nj;
@@ -745,14 +682,16 @@ struct AssocWarp {
     float4* dt;      // [wd] d0 table of the item's columns
     uint32_t* cur;   // [cap] row cursors of the pass's peaks (offsets from the pass's first row)
     uint2* ring;     // [assoc_ring(rows)] (column << 16 | kappa bin, hit)
+    uint2* hq;       // [kHitQueue] (hit, d0 band bits) of banded hits
     uint32_t* mask;  // [rows * wd][nkw] peak bits of the item's columns
-    uint32_t* nearb; // [rows * wd][nkw] bins within `window` of a peak
+    uint32_t* nearb; // [rows * wd][nk / 32 + 1] bins within `window` of a peak; bin nk (no bin) is 0
     int32_t* lpre;   // [rows * wd][nkw] item-local id of the first peak of each word
 };
 
 __host__ __device__ inline size_t assoc_warp_bytes(int rows, int wd, int nk, int cap) {
-    const size_t nkw = (nk + 31) / 32;
-    return ((16 * (size_t)wd + 4 * (size_t)cap + 8 * (size_t)assoc_ring(rows) + 12 * (size_t)rows * wd * nkw) +
+    const size_t nkw = (nk + 31) / 32, nkn = nk / 32 + 1;
+    return ((16 * (size_t)wd + 4 * (size_t)cap + 8 * (size_t)(assoc_ring(rows) + kHitQueue) +
+             4 * (size_t)rows * wd * (2 * nkw + nkn)) +
             15) &
            ~size_t(15);
 }
@@ -834,15 +773,97 @@ __device__ __forceinline__ void assoc_drain(const AssocParams& p, const AssocWar
     __syncwarp();  // entries read before the ring slots are reused
 }
 
+// One warp's 32 hits (lane i: hit hh, `valid`) against the item's columns in
+// jm: certified bins, near test, and ring pushes with drains.
+template <int SPHI, int NK, int RING>
+__device__ __forceinline__ void assoc_cells(const AssocParams& p, const AssocWarp& S, const AssocPass& ps,
+                                            const float* cp, const float* sp, float x, float y, int64_t hh,
+                                            bool valid, unsigned jm, unsigned cmask, int WD, int nk, int nkw, int nkn,
+                                            int lane, unsigned lt, unsigned& head, unsigned& tail) {
+    constexpr int U = assoc_unroll(SPHI);
+    const unsigned nku = (unsigned)nk;
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    const HitFast hf = hit_fast(x, y, p.K);
+    float q_[SPHI], qs[SPHI];
+#pragma unroll
+    for (int r = 0; r < SPHI; ++r) {
+        q_[r] = q_of(x, y, cp[r], sp[r]);
+        qs[r] = q_[r] * S2;
+    }
+    // U columns per step, SPHI rows each: independent cells for the
+    // pipelines; steps past the last active column repeat column
+    // jj[0] with its cells masked off
+    while (jm) {
+        int jj[U];
+        bool jv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            jv[u] = jm != 0u;
+            jj[u] = jv[u] ? __ffs(jm) - 1 : jj[0];
+            jm &= jm - 1u;
+        }
+        unsigned kb[U][SPHI];  // the bin, or nk for none
+        bool und_any = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float4 dt = S.dt[jj[u]];
+            const float Rj = hf.r2 + dt.z;
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                const int c = r * WD + jj[u];
+                const bool on = valid && jv[u] && (SPHI == 1 || ((cmask >> c) & 1u));
+                const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+                kb[u][r] = ((o.flo == o.fhi) & on) ? min(o.kb, nku) : nku;
+                und_any |= (o.flo != o.fhi) & on;
+            }
+        }
+        if (__any_sync(0xffffffffu, und_any)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float4 dt = S.dt[jj[u]];
+                const float Rj = hf.r2 + dt.z;
+#pragma unroll
+                for (int r = 0; r < SPHI; ++r) {
+                    const int c = r * WD + jj[u];
+                    const bool on = valid && jv[u] && (SPHI == 1 || ((cmask >> c) & 1u));
+                    const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
+                    if ((o.flo != o.fhi) && on && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi)) {
+                        const int ks = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                        kb[u][r] = ks >= 0 ? (unsigned)ks : nku;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                const int c = r * WD + jj[u];
+                const unsigned b = kb[u][r];
+                const bool cand = (S.nearb[c * nkn + (b >> 5)] >> (b & 31)) & 1u;
+                const unsigned m = __ballot_sync(0xffffffffu, cand);
+                if (cand)
+                    S.ring[(tail + __popc(m & lt)) & (RING - 1)] =
+                        make_uint2(((unsigned)c << 16) | b, (unsigned)hh);
+                tail += __popc(m);
+            }
+        }
+        while (tail - head >= 32) {
+            assoc_drain<RING>(p, S, nkw, nk, head, 32, ps, lane);
+            head += 32;
+        }
+    }
+}
+
 template <int SPHI, int NK, bool BAND>
 __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = NK ? NK : p.K.nk;
     const int nkw = (nk + 31) >> 5;
+    const int nkn = (nk >> 5) + 1;  // near words per column, the last holding bin nk
     const int WD = p.wd;
     const int ncols = SPHI * WD;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int U = assoc_unroll(SPHI);
     constexpr int RING = assoc_ring(SPHI);
     AssocWarp S;
     {
@@ -851,18 +872,18 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p) {
         ptr += 16 * WD;
         S.ring = reinterpret_cast<uint2*>(ptr);
         ptr += 8 * RING;
+        S.hq = reinterpret_cast<uint2*>(ptr);
+        ptr += 8 * kHitQueue;
         S.cur = reinterpret_cast<uint32_t*>(ptr);
         ptr += 4 * p.cap;
         S.mask = reinterpret_cast<uint32_t*>(ptr);
-        S.nearb = S.mask + ncols * nkw;
-        S.lpre = reinterpret_cast<int32_t*>(S.nearb + ncols * nkw);
+        S.lpre = reinterpret_cast<int32_t*>(S.mask + ncols * nkw);
+        S.nearb = reinterpret_cast<uint32_t*>(S.lpre + ncols * nkw);
     }
     const int tiles_phi = (p.K.nphi + SPHI - 1) / SPHI;
     const int tiles_d = (p.K.nd + WD - 1) / WD;
     const int64_t tiles = (int64_t)tiles_phi * tiles_d;
     const int64_t n_items = (int64_t)p.n_events * tiles;
-    const unsigned nku = (unsigned)nk;
-    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
     const unsigned lt = lanemask_lt();
     for (;;) {
         unsigned long long it = 0;
@@ -897,13 +918,14 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p) {
         }
         if (lane < nj) S.dt[lane] = p.dtab[j0 + lane];
         __syncwarp();
-        for (int v = lane; v < ncols * nkw; v += 32) {
-            const int w = v - (v / nkw) * nkw;
-            const uint32_t* m = S.mask + (v - w);
-            uint32_t nb = m[w];
-            const uint32_t hi_w = w + 1 < nkw ? m[w + 1] : 0u, lo_w = w > 0 ? m[w - 1] : 0u;
-            for (int o = 1; o <= p.window; ++o)
-                nb |= (m[w] >> o) | (hi_w << (32 - o)) | (m[w] << o) | (lo_w >> (32 - o));
+        for (int v = lane; v < ncols * nkn; v += 32) {
+            const int c = v / nkn, w = v - (v / nkn) * nkn;
+            const uint32_t* m = S.mask + c * nkw;
+            const uint32_t mw = w < nkw ? m[w] : 0u;
+            const uint32_t hi_w = w + 1 < nkw ? m[w + 1] : 0u, lo_w = w > 0 && w - 1 < nkw ? m[w - 1] : 0u;
+            uint32_t nb = mw;
+            for (int o = 1; o <= p.window; ++o) nb |= (mw >> o) | (hi_w << (32 - o)) | (mw << o) | (lo_w >> (32 - o));
+            if (w == (nk >> 5)) nb &= (1u << (nk & 31)) - 1u;  // no bins from nk on
             S.nearb[v] = nb;
         }
         float cp[SPHI], sp[SPHI];
@@ -936,97 +958,73 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p) {
             jmask &= (unsigned)((1ull << nj) - 1ull);
             unsigned head = 0, tail = 0;
             __syncwarp();
-            int64_t hh = hb + lane;
-            float xn = hh < he ? p.x[hh] : 0.0f;
-            float yn = hh < he ? p.y[hh] : 0.0f;
-            for (int64_t h0 = hb; h0 < he; h0 += 32, hh += 32) {
-                const bool valid = hh < he;
-                const float x = xn, y = yn;
-                if (hh + 32 < he) {  // next chunk's coordinates
-                    xn = p.x[hh + 32];
-                    yn = p.y[hh + 32];
+            if (!BAND) {
+                int64_t hh = hb + lane;
+                float xn = hh < he ? p.x[hh] : 0.0f;
+                float yn = hh < he ? p.y[hh] : 0.0f;
+                for (int64_t h0 = hb; h0 < he; h0 += 32, hh += 32) {
+                    const float x = xn, y = yn;
+                    if (hh + 32 < he) {  // next chunk's coordinates
+                        xn = p.x[hh + 32];
+                        yn = p.y[hh + 32];
+                    }
+                    assoc_cells<SPHI, NK, RING>(p, S, ps, cp, sp, x, y, hh, hh < he, jmask, cmask, WD, nk, nkw, nkn,
+                                                lane, lt, head, tail);
                 }
-                const HitFast hf = hit_fast(x, y, p.K);
-                float q_[SPHI], qs[SPHI];
-#pragma unroll
-                for (int r = 0; r < SPHI; ++r) {
-                    q_[r] = q_of(x, y, cp[r], sp[r]);
-                    qs[r] = q_[r] * S2;
-                }
-                unsigned jm = jmask;
-                if (BAND) {
-                    // union of the lanes' d0 bands: columns outside it cannot vote
-                    unsigned bm = 0;
+            } else {
+                // hits whose d0 band misses the pass's columns are dropped; the
+                // rest queue in hit order and run 32 at a time over the union
+                // of their bands
+                unsigned qh = 0, qt = 0;
+                for (int64_t h0 = hb; h0 < he; h0 += 32) {
+                    const int64_t hh = h0 + lane;
+                    const bool valid = hh < he;
+                    const float x = valid ? p.x[hh] : 0.0f;
+                    const float y = valid ? p.y[hh] : 0.0f;
+                    const float r2 = fmaf(x, x, __fmul_rn(y, y));
+                    int lo = nj, hi = -1;
 #pragma unroll
                     for (int r = 0; r < SPHI; ++r) {
-                        int jlo, jhi;
-                        d0_band(hf.r2, q_[r], dlo, dhi, j0, nj, p.K, jlo, jhi);
-                        if (valid && jhi >= jlo)
-                            bm |= (unsigned)(((2ull << (jhi - j0)) - 1ull) & ~((1ull << (jlo - j0)) - 1ull));
+                        int jl, jh;
+                        d0_band(r2, q_of(x, y, cp[r], sp[r]), dlo, dhi, j0, nj, p.K, jl, jh);
+                        if (jh >= jl) {
+                            lo = min(lo, jl - j0);
+                            hi = max(hi, jh - j0);
+                        }
                     }
-                    jm &= __reduce_or_sync(0xffffffffu, bm);
+                    const unsigned bits =
+                        hi >= lo ? (0xFFFFFFFFu >> (31 - (hi - lo))) << lo & jmask : 0u;
+                    const bool keep = valid && bits != 0u;
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep) S.hq[(qt + __popc(m & lt)) & (kHitQueue - 1)] = make_uint2((unsigned)hh, bits);
+                    qt += __popc(m);
+                    if (qt - qh >= 32) {
+                        const int n = 32;
+                        __syncwarp();
+                        const bool has = lane < n;
+                        const uint2 ent = has ? S.hq[(qh + lane) & (kHitQueue - 1)] : make_uint2(0u, 0u);
+                        const unsigned jm = __reduce_or_sync(0xffffffffu, ent.y);
+                        __syncwarp();  // entries read before their slots are reused
+                        qh += n;
+                        const float qx = has ? p.x[ent.x] : 0.0f;
+                        const float qy = has ? p.y[ent.x] : 0.0f;
+                        assoc_cells<SPHI, NK, RING>(p, S, ps, cp, sp, qx, qy, (int64_t)ent.x, has, jm, cmask, WD, nk,
+                                                    nkw, nkn, lane, lt, head, tail);
+                    }
                 }
-                // U columns per step, SPHI rows each: independent cells for the
-                // pipelines; steps past the last active column repeat column
-                // jj[0] with its cells masked off
-                while (jm) {
-                    int jj[U];
-                    bool jv[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        jv[u] = jm != 0u;
-                        jj[u] = jv[u] ? __ffs(jm) - 1 : jj[0];
-                        jm &= jm - 1u;
-                    }
-                    int kb[U][SPHI];
-                    bool und_any = false;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const float4 dt = S.dt[jj[u]];
-                        const float Rj = hf.r2 + dt.z;
-#pragma unroll
-                        for (int r = 0; r < SPHI; ++r) {
-                            const int c = r * WD + jj[u];
-                            const bool on = valid && jv[u] && (SPHI == 1 || ((cmask >> c) & 1u));
-                            const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
-                            kb[u][r] = ((o.flo == o.fhi) & (o.kb < nku) & on) ? (int)o.kb : -1;
-                            und_any |= (o.flo != o.fhi) & on;
-                        }
-                    }
-                    if (__any_sync(0xffffffffu, und_any)) {
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const float4 dt = S.dt[jj[u]];
-                            const float Rj = hf.r2 + dt.z;
-#pragma unroll
-                            for (int r = 0; r < SPHI; ++r) {
-                                const int c = r * WD + jj[u];
-                                const bool on = valid && jv[u] && (SPHI == 1 || ((cmask >> c) & 1u));
-                                const S1 o = stage1_fast(qs[r], q_[r], dt, Rj, hf.G, H, T0);
-                                if ((o.flo != o.fhi) && on && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi))
-                                    kb[u][r] = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-#pragma unroll
-                        for (int r = 0; r < SPHI; ++r) {
-                            const int c = r * WD + jj[u];
-                            const int b = kb[u][r];
-                            const uint32_t nb = S.nearb[c * nkw + (b >= 0 ? (b >> 5) : 0)];
-                            const bool cand = b >= 0 && ((nb >> (b & 31)) & 1u);
-                            const unsigned m = __ballot_sync(0xffffffffu, cand);
-                            if (cand)
-                                S.ring[(tail + __popc(m & lt)) & (RING - 1)] =
-                                    make_uint2(((unsigned)c << 16) | (unsigned)b, (unsigned)hh);
-                            tail += __popc(m);
-                        }
-                    }
-                    while (tail - head >= 32) {
-                        assoc_drain<RING>(p, S, nkw, nk, head, 32, ps, lane);
-                        head += 32;
-                    }
+                // at most 31 left once the last chunk was queued
+                if (qt != qh) {
+                    const int n = (int)(qt - qh);
+                    __syncwarp();
+                    const bool has = lane < n;
+                    const uint2 ent = has ? S.hq[(qh + lane) & (kHitQueue - 1)] : make_uint2(0u, 0u);
+                    const unsigned jm = __reduce_or_sync(0xffffffffu, ent.y);
+                    __syncwarp();
+                    qh += n;
+                    const float qx = has ? p.x[ent.x] : 0.0f;
+                    const float qy = has ? p.y[ent.x] : 0.0f;
+                    assoc_cells<SPHI, NK, RING>(p, S, ps, cp, sp, qx, qy, (int64_t)ent.x, has, jm, cmask, WD, nk,
+                                                nkw, nkn, lane, lt, head, tail);
                 }
             }
             if (tail != head) assoc_drain<RING>(p, S, nkw, nk, head, (int)(tail - head), ps, lane);
@@ -1062,8 +1060,8 @@ __global__ void rcp_check_kernel(uint32_t first_bits, uint32_t count, unsigned l
 // launchers
 // ---------------------------------------------------------------------------
 int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band) {
-    const int chunk = band ? threads * (4 + 4 + 4 + 2 * kBuckets) + 4 : 0;
-    return 16 * tile_d + chunk + 4 * tile_phi * tile_d * nk;
+    const int queues = band ? (threads / 32) * kHitQueue * 8 : 0;
+    return 16 * tile_d + queues + 4 * tile_phi * tile_d * nk;
 }
 
 

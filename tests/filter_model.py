@@ -162,21 +162,27 @@ def band_consts(grid, d0):
                 idd=F(grid.n_d0 / (float(F(grid.d0_max)) - float(F(grid.d0_min)))), big=F(1e30))
 
 
-def band(x, y, c, s, j0, nj, d0, C):
-    """[jlo, jhi] (inclusive, clipped to the tile [j0, j0 + nj)) in float32; jhi < jlo if empty."""
+def band(x, y, c, s, j0, nj, d0, C, tilt=(0, 0, 0, 0)):
+    """[jlo, jhi] (inclusive, clipped to the tile [j0, j0 + nj)) in float32; jhi < jlo if empty.
+
+    The kernels take the square roots and the reciprocals approximately (a
+    few ulps); `tilt` = signs (-1, 0, +1) by which sqrt(DA), sqrt(DB), a1 and
+    b2 are pushed by a relative 2^-20, beyond those errors, so that a test can
+    hold the band to the superset property in the adversarial directions."""
     x, y, c, s = (np.asarray(v, F) for v in (x, y, c, s))
+    e = [F(1.0 + t * 2.0 ** -20) for t in tilt]
     with np.errstate(all="ignore"):
         r2 = fma(x, x, y * y)
         q = fma(y, c, -(x * s))
         p2 = np.maximum(fma(-q, q, r2), F(0))
         DA = fma(-C["A2"], p2, F(1))
         DB = fma(-C["B2"], p2, F(1))
-        sA = np.sqrt(np.maximum(DA, F(0)))
-        sB = np.sqrt(np.maximum(DB, F(0)))
+        sA = np.sqrt(np.maximum(DA, F(0))) * e[0]
+        sB = np.sqrt(np.maximum(DB, F(0))) * e[1]
         # forbidden (a1, a2) where kappa < A, [b1, b2] where kappa > B (empty when D <= 0)
-        a1 = np.where(DA > 0, (C["A2"] * p2) * C["iA"] / (F(1) + sA), C["big"])
+        a1 = np.where(DA > 0, (C["A2"] * p2) * C["iA"] / (F(1) + sA) * e[2], C["big"])
         a2 = np.where(DA > 0, (F(1) + sA) * C["iA"], C["big"])
-        b2 = np.where(DB > 0, -(C["B2"] * p2) * C["iB"] / (F(1) + sB), -C["big"])
+        b2 = np.where(DB > 0, -(C["B2"] * p2) * C["iB"] / (F(1) + sB) * e[3], -C["big"])
         b1 = np.where(DB > 0, -(F(1) + sB) * C["iB"], -C["big"])
         ulo = F(d0[j0]) - q
         uhi = F(d0[j0 + nj - 1]) - q

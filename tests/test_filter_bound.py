@@ -94,7 +94,9 @@ def test_stage1_and_stage2_never_disagree_with_binary64(oracle_mod, wname):
                                    "pileup_64x5000trk"])
 def test_d0_band_contains_every_voting_column(oracle_mod, wname):
     """The pruned vote evaluates only the d0 band of each (hit, phi row); every
-    column where the hit votes in binary64 must lie inside it."""
+    column where the hit votes in binary64 must lie inside it, also with the
+    band's roots pushed beyond the errors of the approximate square roots and
+    reciprocals the kernels use."""
     w = synth.WORKLOADS[wname]
     g = w.grid
     b = synth.generate(w, n_events=1, first_event=5)
@@ -109,12 +111,15 @@ def test_d0_band_contains_every_voting_column(oracle_mod, wname):
     ci = np.tile(c[rows], nh)
     si = np.tile(s[rows], nh)
     frac = []
+    tilts = ((0, 0, 0, 0), (1, 1, 1, 1), (-1, -1, -1, -1), (1, -1, -1, 1), (-1, 1, 1, -1))
     for j0, nj in ((0, g.n_d0), (0, max(1, g.n_d0 // 2)), (g.n_d0 // 4, max(1, g.n_d0 // 4))):
-        jlo, jhi = fm.band(x, y, ci, si, j0, nj, d, C)
-        for j in range(j0, j0 + nj):
-            k = oracle_mod.kbin_cells(g, x, y, ci, si, np.full(x.shape, d[j], np.float32))
-            votes = k >= 0
-            outside = votes & ((j < jlo) | (j > jhi))
-            assert not outside.any(), (j, np.nonzero(outside)[0][:5])
-        frac.append(np.maximum(jhi - jlo + 1, 0).mean() / nj)
+        votes = {j: oracle_mod.kbin_cells(g, x, y, ci, si, np.full(x.shape, d[j], np.float32)) >= 0
+                 for j in range(j0, j0 + nj)}
+        for tilt in tilts:
+            jlo, jhi = fm.band(x, y, ci, si, j0, nj, d, C, tilt)
+            for j in range(j0, j0 + nj):
+                outside = votes[j] & ((j < jlo) | (j > jhi))
+                assert not outside.any(), (tilt, j, np.nonzero(outside)[0][:5])
+            if tilt == tilts[0]:
+                frac.append(np.maximum(jhi - jlo + 1, 0).mean() / nj)
     assert frac[0] < 0.45, frac
