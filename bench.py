@@ -34,6 +34,12 @@ WORKLOAD = "batch_4096_lognormal"
 METRIC = "events/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one launch on the 512-event case of the batch
+# workload, from ncu (profiles/assoc_kernel_batch512.md: 1.2365 + 2.3600 GB;
+# profiles/vote_band_kernel_batch512.md: 0.0197 + 2.0874 GB); set to None when
+# the kernel changes until it is captured again
+ASSOC_DRAM_512 = (1.236538 + 2.360003) * 1e9
+VOTE_DRAM_512 = (0.019719 + 2.087443) * 1e9
 
 
 def _dist():
@@ -232,7 +238,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, vote_ms, rest_ms = [], [], []
+    step_ms, vote_ms, rest_ms, assoc_ms = [], [], [], []
     with ClockSampler(torch.cuda.current_device()) as clocks:
         for _ in range(args.steps):
             flush.fill_(1.0)  # evict L2 between timed steps
@@ -243,9 +249,10 @@ def run_gpu(args):
             e1.record(stream)
             ctx.sync()
             step_ms.append(e0.elapsed_time(e1))
-            v, r, _ = ctx.phase_times()
+            v, r, _, a = ctx.phase_times()
             vote_ms.append(v)
             rest_ms.append(r)
+            assoc_ms.append(a)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -262,7 +269,8 @@ def run_gpu(args):
                               "workload": args.workload, "hit_votes_per_s": world * hit_votes / (ms / 1e3),
                               "prune": ctx.get_option(ht.HT_OPT_PRUNE),
                               "events": n_events, "phase_ms": {"vote": float(np.mean(vote_ms)),
-                                                               "peaks_assoc": float(np.mean(rest_ms))},
+                                                               "peaks_assoc": float(np.mean(rest_ms)),
+                                                               "assoc": float(np.mean(assoc_ms))},
                               "peaks": int(counts[0]), "pairs": int(counts[1]), "tile": tile}), flush=True)
         ctx.close()
         return 0
@@ -331,20 +339,26 @@ def run_gpu(args):
         except Exception as e:  # report, do not hide, a failing loop
             serving = {"error": f"{type(e).__name__}: {e}"}
 
-    # ---- roofline of the dominant kernel (vote): issue-bound ALU work
+    # ---- roofline of the dominant kernel (association) and of the vote:
+    # issue-bound ALU work, 6 ops per (hit, phi0, d0) cell of the method
     peaks, peak_src = _peaks()
     clk = clocks.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     vote_s = float(np.mean(vote_ms)) / 1e3
+    assoc_s = float(np.mean(assoc_ms)) / 1e3
     ops_per_cell = 6  # add, fma, reciprocal, multiply, fma, bin test: the formula's minimum per cell
-    # DRAM read + write of the vote kernel from ncu on the 512-event case of this
-    # workload (profiles/vote_kernel_batch512.md: 0.0186 + 2.0867 GB), scaled to a
-    # full launch by the events processed (the traffic is the accumulator write)
-    vote_traffic = (0.018555 + 2.086702) * 1e9 * n_events / 512
     cells_per_launch = hit_votes
-    achieved = ops_per_cell * cells_per_launch / vote_s / 1e12
+    achieved = ops_per_cell * cells_per_launch / assoc_s / 1e12
+    achieved_vote = ops_per_cell * cells_per_launch / vote_s / 1e12
     peak_tops = sms * 128 * sm_mhz * 1e6 / 1e12
+    # DRAM read + write per launch from ncu on the 512-event case of this
+    # workload (profiles/*_batch512.md), scaled to a full launch by the hits
+    # processed; None where the kernel changed after the capture
+    hits512 = 2108472
+    assoc_traffic = ASSOC_DRAM_512 * n_hits / hits512 if ASSOC_DRAM_512 else None
+    vote_traffic = VOTE_DRAM_512 * n_hits / hits512 if VOTE_DRAM_512 else None
+    peak_basis = f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"
     acc_bytes = 4.0 * g.n_phi * g.n_d0 * g.n_kappa * n_events
     line = {
         "metric": METRIC, "value": world * n_events / (ms / 1e3), "unit": METRIC, "n_gpus": world,
@@ -358,11 +372,14 @@ def run_gpu(args):
         "peaks_per_step": int(counts[0]), "pairs_per_step": int(counts[1]),
         "plain_events_per_s": plain_eps,
         "batched_over_plain": (n_events / (ms / 1e3)) / plain_eps,
-        "phase_ms": {"vote": float(np.mean(vote_ms)), "peaks_assoc": float(np.mean(rest_ms))},
+        "phase_ms": {"vote": float(np.mean(vote_ms)), "peaks_assoc": float(np.mean(rest_ms)),
+                     "assoc": float(np.mean(assoc_ms))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops, "traffic": vote_traffic,
-                     "kernel": "vote_kernel", "ops_per_cell": ops_per_cell,
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"},
+                     "frac": achieved / peak_tops, "traffic": assoc_traffic,
+                     "kernel": "assoc_kernel", "ops_per_cell": ops_per_cell, "peak_basis": peak_basis},
+        "roofline_vote": {"bound": "alu", "achieved": achieved_vote, "peak": peak_tops, "unit": "Tops/s",
+                          "frac": achieved_vote / peak_tops, "traffic": vote_traffic,
+                          "kernel": "vote_band_kernel", "ops_per_cell": ops_per_cell, "peak_basis": peak_basis},
         "hbm": {"step_bytes_min": 2 * acc_bytes + 8.0 * n_hits,
                 "achieved_gbs": (2 * acc_bytes + 8.0 * n_hits) / (ms / 1e3) / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src},

@@ -203,8 +203,9 @@ int ht_sync(ht_ctx *ctx);
 int ht_autotune(ht_ctx *ctx, const ht_hits *hits, void *stream);
 
 /* Device time of the last single-wave ht_process (needs HT_OPT_PHASE_TIMING=1,
- * read after ht_sync): ms[0] vote kernel, ms[1] peaks + association, ms[2]
- * whole device step.  Events are recorded on the step's stream, so the
+ * read after ht_sync), into ms[4]: ms[0] vote kernel, ms[1] peaks +
+ * association, ms[2] whole device step, ms[3] association kernel (with its
+ * work-counter reset).  Events are recorded on the step's stream, so the
  * numbers hold inside a replayed CUDA graph too. */
 int ht_phase_times(ht_ctx *ctx, float *ms);
 

@@ -132,8 +132,8 @@ struct ht_ctx {
 
     // optional per-phase device timing (external events, also inside graphs)
     bool timing = false;
-    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
-    float phase_ms[3] = {0, 0, 0};
+    cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float phase_ms[4] = {0, 0, 0, 0};
     int64_t launches = 0;  // kernels issued by the last ht_process
 
     std::string last_error;
@@ -522,8 +522,11 @@ int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, co
 }
 
 // pair offsets for this wave's peaks [d_scal[2], d_scal[0]) clamped to cap, and association
+int mark(ht_ctx* ctx, int which, cudaStream_t s);
+
 int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* order, int64_t peak_cap,
-                    int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, cudaStream_t s) {
+                    int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, bool timed,
+                    cudaStream_t s) {
     CU(cudaMemcpyAsync(ctx->d_scal + 3, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     ScanRange r{};
     r.in = ctx->paircnt.p;
@@ -541,6 +544,10 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* orde
     a.hit_idx = hit_idx;
     a.pair_cap = pair_cap;
     a.window = window;
+    if (timed) {
+        const int st = mark(ctx, 4, s);
+        if (st) return st;
+    }
     return launch_assoc_ctx(ctx, a, event0, ne, order, s);
 }
 
@@ -591,7 +598,7 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
         if (st) return st;
         CU(launch_emit(pp, s));
         st = run_pairs_assoc(ctx, e0, ne, plain ? nullptr : ctx->order.p, peak_cap, peak_offsets, hit_idx, pair_cap,
-                             window, s);
+                             window, single, s);
         if (st) return st;
         if (single && (st = mark(ctx, 2, s))) return st;
         ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1;
@@ -1024,6 +1031,7 @@ int ht_sync(ht_ctx* ctx) {
         if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[1]) == cudaSuccess) ctx->phase_ms[0] = ms;
         if (cudaEventElapsedTime(&ms, ctx->tev[1], ctx->tev[2]) == cudaSuccess) ctx->phase_ms[1] = ms;
         if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[3]) == cudaSuccess) ctx->phase_ms[2] = ms;
+        if (cudaEventElapsedTime(&ms, ctx->tev[4], ctx->tev[2]) == cudaSuccess) ctx->phase_ms[3] = ms;
         cudaGetLastError();
     }
     int st = read_err(ctx);
@@ -1059,7 +1067,7 @@ int ht_get_tables(ht_ctx* ctx, float* cos_phi, float* sin_phi, float* d0) {
 int ht_phase_times(ht_ctx* ctx, float* ms) {
     if (!ctx || !ms) return HT_ERR_INVALID_ARG;
     if (!ctx->timing) return fail(ctx, HT_ERR_STATE, "HT_OPT_PHASE_TIMING is off");
-    for (int i = 0; i < 3; ++i) ms[i] = ctx->phase_ms[i];
+    for (int i = 0; i < 4; ++i) ms[i] = ctx->phase_ms[i];
     return HT_OK;
 }
 

@@ -334,9 +334,10 @@ def ht_filter_stats(ctx, reset=False):
 
 
 def ht_phase_times(ctx):
-    ms = np.zeros(3, np.float32)
+    """(vote, peaks + association, whole step, association kernel) in ms."""
+    ms = np.zeros(4, np.float32)
     _check(load().ht_phase_times(ctx, ms.ctypes.data), ctx)
-    return float(ms[0]), float(ms[1]), float(ms[2])
+    return float(ms[0]), float(ms[1]), float(ms[2]), float(ms[3])
 
 
 def ht_peaks_noalloc(grid, acc, n_events, threshold, peaks, cap, count, stream=None):
