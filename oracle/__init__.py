@@ -64,6 +64,12 @@ def lib():
             "hto_associate": (i64, [G, P, P, P, P, i64, i32, P, P, i64]),
             "hto_flip_count": (None, [G, P, P, P, i32, P]),
             "hto_run_events": (None, [G, P, P, P, i32, u32, i32, i32, P]),
+            "hto_edges": (None, [G, P, P, P]),
+            "hto_code_at": (i32, [G, f, f, f, f, f]),
+            "hto_code_cells": (None, [G, i64, P, P, P, P, P, P]),
+            "hto_range": (i32, [G, f, f, i32, i32, P, P]),
+            "hto_vote_range": (None, [G, P, P, P, i32, P]),
+            "hto_associate_range": (i64, [G, P, P, P, P, i64, i32, P, P, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -201,3 +207,68 @@ def run_events(g, x, y, event_offsets, threshold, window, n_threads):
     lib().hto_run_events(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(offs), offs.shape[0] - 1,
                          int(threshold), int(window), int(n_threads), _ptr(out))
     return int(out[0]), int(out[1]), int(out[2])
+
+
+# ---- range voting --------------------------------------------------------
+
+UNDEF = -2  # corner code when the corner's denominator is not positive
+
+
+def edges(g):
+    """(cos, sin) of the phi0 edges m 2pi/n_phi and the n_d0 + 1 d0 edges (float32)."""
+    gs = grid_struct(g)
+    c = np.empty(gs.n_phi, np.float32)
+    s = np.empty(gs.n_phi, np.float32)
+    d = np.empty(gs.n_d0 + 1, np.float32)
+    lib().hto_edges(ctypes.byref(gs), _ptr(c), _ptr(s), _ptr(d))
+    return c, s, d
+
+
+def code_at(g, x, y, c, s, d) -> int:
+    return int(lib().hto_code_at(ctypes.byref(grid_struct(g)), float(x), float(y), float(c), float(s), float(d)))
+
+
+def code_cells(g, x, y, c, s, d) -> np.ndarray:
+    """Corner codes (UNDEF, -1 below, n_kappa above, else the bin) over equal-length arrays."""
+    gs = grid_struct(g)
+    x, y, c, s, d = (_f32(v) for v in (x, y, c, s, d))
+    out = np.empty(x.shape[0], np.int32)
+    lib().hto_code_cells(ctypes.byref(gs), x.shape[0], _ptr(x), _ptr(y), _ptr(c), _ptr(s), _ptr(d), _ptr(out))
+    return out
+
+
+def range_of(g, x, y, i, j):
+    """(lo, hi) bins hit (x, y) votes for in cell (i, j) under range voting, or None."""
+    lo = ctypes.c_int32()
+    hi = ctypes.c_int32()
+    ok = lib().hto_range(ctypes.byref(grid_struct(g)), float(x), float(y), int(i), int(j),
+                         ctypes.byref(lo), ctypes.byref(hi))
+    return (lo.value, hi.value) if ok else None
+
+
+def vote_range(g, x, y, event_offsets=None) -> np.ndarray:
+    """Range-vote accumulators [n_events, n_phi, n_d0, n_kappa] uint32."""
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    offs = _offs(event_offsets, x.shape[0])
+    ne = offs.shape[0] - 1
+    acc = np.empty((ne, gs.n_phi, gs.n_d0, gs.n_kappa), dtype=np.uint32)
+    lib().hto_vote_range(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(offs), ne, _ptr(acc))
+    return acc
+
+
+def associate_range(g, x, y, event_offsets, pk, window):
+    """Range association CSR (peak_offsets int64[n_peaks+1], hit_idx int32[n_pairs])."""
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    offs = _offs(event_offsets, x.shape[0])
+    pk = np.ascontiguousarray(pk, dtype=PEAK_DTYPE)
+    po = np.empty(pk.shape[0] + 1, np.int64)
+    cap = 1 << 16
+    while True:
+        hi = np.empty(cap, np.int32)
+        n = lib().hto_associate_range(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(offs), _ptr(pk), pk.shape[0],
+                                      int(window), _ptr(po), _ptr(hi), cap)
+        if n <= cap:
+            return po, hi[:n].copy()
+        cap = n

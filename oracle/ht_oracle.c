@@ -322,3 +322,144 @@ void hto_run_events(const hto_grid *g, const float *x, const float *y,
     free(args);
     free(th);
 }
+
+/* ---- range voting (the first extension beyond the point vote) -------------
+ *
+ * Section 3 lets a hit vote for every instance containing it.  With point
+ * sampling, an instance (cell) contains the hit when the hit's curve passes
+ * through the cell's centre column; range voting instead takes every kappa
+ * bin the curve crosses over the whole (phi0, d0) cell.  Reading used here:
+ * the curve's kappa is evaluated, by the binary64 definition above, at the
+ * cell's four corners (phi0 edges m 2pi/n_phi, periodic; d0 edges
+ * d0_min + n (d0_max - d0_min)/n_d0), and the hit votes for every bin from
+ * the lowest to the highest corner bin, clipped to [0, n_kappa).  A corner
+ * whose denominator is not positive (the hit is that corner's perigee point)
+ * leaves the cell without a vote.
+ */
+
+/* Edge tables: cos/sin of m 2pi/n_phi for m = 0..n_phi-1 and the n_d0 + 1
+ * d0 edges, each rounded to float once. */
+void hto_edges(const hto_grid *g, float *cos_e, float *sin_e, float *d_e)
+{
+    for (int32_t m = 0; m < g->n_phi; ++m) {
+        double phi = (double)m * (2.0 * kPi / (double)g->n_phi);
+        cos_e[m] = (float)cos(phi);
+        sin_e[m] = (float)sin(phi);
+    }
+    for (int32_t n = 0; n <= g->n_d0; ++n) {
+        double w = ((double)g->d0_max - (double)g->d0_min) / (double)g->n_d0;
+        d_e[n] = (float)((double)g->d0_min + (double)n * w);
+    }
+}
+
+/* Corner code: HTO_UNDEF when den <= 0, -1 below the kappa range, n_kappa
+ * above it, else the bin. */
+int32_t hto_code_at(const hto_grid *g, float x, float y, float c, float s, float d)
+{
+    double w = hto_w64(g, x, y, c, s, d);
+    if (isnan(w))
+        return HTO_UNDEF;
+    if (w < 0.0)
+        return -1;
+    if (w >= (double)g->n_kappa)
+        return g->n_kappa;
+    return (int32_t)w;
+}
+
+void hto_code_cells(const hto_grid *g, int64_t n, const float *x, const float *y, const float *c,
+                    const float *s, const float *d, int32_t *out)
+{
+    for (int64_t t = 0; t < n; ++t)
+        out[t] = hto_code_at(g, x[t], y[t], c[t], s[t], d[t]);
+}
+
+/* Bins [*lo, *hi] (clipped) that hit (x, y) votes for in cell (i, j); returns
+ * 0 when it votes for none. */
+static int range_cell(const hto_grid *g, const float *ce, const float *se, const float *de,
+                      float x, float y, int32_t i, int32_t j, int32_t *lo, int32_t *hi)
+{
+    int32_t i1 = (i + 1) % g->n_phi;
+    int32_t code[4];
+    code[0] = hto_code_at(g, x, y, ce[i], se[i], de[j]);
+    code[1] = hto_code_at(g, x, y, ce[i1], se[i1], de[j]);
+    code[2] = hto_code_at(g, x, y, ce[i], se[i], de[j + 1]);
+    code[3] = hto_code_at(g, x, y, ce[i1], se[i1], de[j + 1]);
+    int32_t a = code[0], b = code[0];
+    for (int t = 0; t < 4; ++t) {
+        if (code[t] == HTO_UNDEF)
+            return 0;
+        if (code[t] < a) a = code[t];
+        if (code[t] > b) b = code[t];
+    }
+    if (b < 0 || a >= g->n_kappa)
+        return 0;
+    *lo = a < 0 ? 0 : a;
+    *hi = b >= g->n_kappa ? g->n_kappa - 1 : b;
+    return 1;
+}
+
+int32_t hto_range(const hto_grid *g, float x, float y, int32_t i, int32_t j, int32_t *lo, int32_t *hi)
+{
+    float *ce = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    float *se = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    float *de = (float *)malloc(sizeof(float) * (size_t)(g->n_d0 + 1));
+    hto_edges(g, ce, se, de);
+    int32_t ok = range_cell(g, ce, se, de, x, y, i, j, lo, hi);
+    free(ce); free(se); free(de);
+    return ok;
+}
+
+void hto_vote_range(const hto_grid *g, const float *x, const float *y,
+                    const int32_t *event_offsets, int32_t n_events, uint32_t *acc)
+{
+    float *ce = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    float *se = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    float *de = (float *)malloc(sizeof(float) * (size_t)(g->n_d0 + 1));
+    hto_edges(g, ce, se, de);
+    const int64_t nd = g->n_d0, nk = g->n_kappa;
+    const int64_t cells = (int64_t)g->n_phi * nd * nk;
+    for (int32_t e = 0; e < n_events; ++e) {
+        uint32_t *a1 = acc + (int64_t)e * cells;
+        memset(a1, 0, sizeof(uint32_t) * (size_t)cells);
+        for (int64_t h = event_offsets[e]; h < event_offsets[e + 1]; ++h)
+            for (int32_t i = 0; i < g->n_phi; ++i)
+                for (int32_t j = 0; j < g->n_d0; ++j) {
+                    int32_t lo, hi;
+                    if (!range_cell(g, ce, se, de, x[h], y[h], i, j, &lo, &hi))
+                        continue;
+                    for (int32_t k = lo; k <= hi; ++k)
+                        a1[((int64_t)i * nd + j) * nk + k] += 1u;
+                }
+    }
+    free(ce); free(se); free(de);
+}
+
+/* Range association: hit h belongs to peak (i, j, k) when its bins in
+ * column (i, j) reach within `window` of k. */
+int64_t hto_associate_range(const hto_grid *g, const float *x, const float *y,
+                            const int32_t *event_offsets, const hto_peak *peaks, int64_t n_peaks,
+                            int32_t window, int64_t *peak_offsets, int32_t *hit_idx, int64_t cap)
+{
+    float *ce = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    float *se = (float *)malloc(sizeof(float) * (size_t)g->n_phi);
+    float *de = (float *)malloc(sizeof(float) * (size_t)(g->n_d0 + 1));
+    hto_edges(g, ce, se, de);
+    int64_t n = 0;
+    peak_offsets[0] = 0;
+    for (int64_t p = 0; p < n_peaks; ++p) {
+        const hto_peak *pk = &peaks[p];
+        for (int64_t h = event_offsets[pk->event]; h < event_offsets[pk->event + 1]; ++h) {
+            int32_t lo, hi;
+            if (!range_cell(g, ce, se, de, x[h], y[h], pk->i_phi, pk->i_d0, &lo, &hi))
+                continue;
+            if (lo <= pk->i_kappa + window && hi >= pk->i_kappa - window) {
+                if (n < cap)
+                    hit_idx[n] = (int32_t)h;
+                ++n;
+            }
+        }
+        peak_offsets[p + 1] = n;
+    }
+    free(ce); free(se); free(de);
+    return n;
+}

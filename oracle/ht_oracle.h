@@ -101,6 +101,34 @@ void hto_run_events(const hto_grid *g, const float *x, const float *y,
                     const int32_t *event_offsets, int32_t n_events,
                     uint32_t threshold, int32_t window, int32_t n_threads, int64_t *out);
 
+/* ---- range voting ----------------------------------------------------------
+ * A hit votes, in cell (i, j), for every kappa bin from the lowest to the
+ * highest bin of its curve at the cell's four corners (phi0 edges
+ * m 2pi/n_phi, periodic; d0 edges d0_min + n (d0_max - d0_min)/n_d0), clipped
+ * to [0, n_kappa); no vote if a corner has den <= 0. */
+#define HTO_UNDEF (-2)
+
+/* Edge tables: cos_e/sin_e[n_phi], d_e[n_d0 + 1]. */
+void hto_edges(const hto_grid *g, float *cos_e, float *sin_e, float *d_e);
+
+/* Corner code: HTO_UNDEF (den <= 0), -1 (below), n_kappa (above) or the bin. */
+int32_t hto_code_at(const hto_grid *g, float x, float y, float c, float s, float d);
+void hto_code_cells(const hto_grid *g, int64_t n, const float *x, const float *y, const float *c,
+                    const float *s, const float *d, int32_t *out);
+
+/* Bins [*lo, *hi] of hit (x, y) in cell (i, j); returns 0 when none. */
+int32_t hto_range(const hto_grid *g, float x, float y, int32_t i, int32_t j, int32_t *lo, int32_t *hi);
+
+/* Range vote of every event (acc as for hto_vote). */
+void hto_vote_range(const hto_grid *g, const float *x, const float *y,
+                    const int32_t *event_offsets, int32_t n_events, uint32_t *acc);
+
+/* Range association: hit h joins peak (i, j, k) when its bins in column
+ * (i, j) reach within `window` of k.  CSR as hto_associate. */
+int64_t hto_associate_range(const hto_grid *g, const float *x, const float *y,
+                            const int32_t *event_offsets, const hto_peak *peaks, int64_t n_peaks,
+                            int32_t window, int64_t *peak_offsets, int32_t *hit_idx, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif
