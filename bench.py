@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -139,6 +140,73 @@ def cpu_baseline(w, batch, budget_s=15.0, max_events=None):
             "sample": f"events 0..{want - 1} of the 4096-event batch ({sub.n_hits} hits), "
                       f"vote+peaks+association, one event per thread", "seconds": dt,
             "hit_votes_per_s": float(sub.n_hits) * w.grid.n_phi * w.grid.n_d0 / dt}
+
+
+def track_efficiency(g, batch, pk, min_hits=8):
+    """(found, findable): tracks with >= min_hits hits whose true (phi0, d0,
+    kappa) lies inside the grid, found when a peak of their event lies within
+    one cell of the true cell in every axis (phi0 periodic)."""
+    dphi = 2 * math.pi / g.n_phi
+    dd = (g.d0_max - g.d0_min) / g.n_d0
+    dk = (g.kappa_max - g.kappa_min) / g.n_kappa
+    ev = pk["event"]
+    found = findable = 0
+    for e in range(batch.n_events):
+        lo, hi = batch.event_offsets[e], batch.event_offsets[e + 1]
+        nh = np.bincount(batch.truth_track[lo:hi][batch.truth_track[lo:hi] >= 0],
+                         minlength=len(batch.truth_params[e]))
+        P = batch.truth_params[e]
+        ok = (nh >= min_hits) & (P[:, 1] >= g.d0_min) & (P[:, 1] < g.d0_max) & (P[:, 2] >= g.kappa_min) & (
+            P[:, 2] < g.kappa_max)
+        if not ok.any():
+            continue
+        i = ((P[ok, 0] % (2 * math.pi)) / dphi).astype(np.int64)
+        j = ((P[ok, 1] - g.d0_min) / dd).astype(np.int64)
+        k = ((P[ok, 2] - g.kappa_min) / dk).astype(np.int64)
+        findable += int(ok.sum())
+        sel = pk[ev == e]
+        if len(sel) == 0:
+            continue
+        di = np.abs(sel["i_phi"][None, :].astype(np.int64) - i[:, None])
+        di = np.minimum(di, g.n_phi - di)
+        near = (di <= 1) & (np.abs(sel["i_d0"][None, :] - j[:, None]) <= 1) & (
+            np.abs(sel["i_kappa"][None, :] - k[:, None]) <= 1)
+        found += int(near.any(axis=1).sum())
+    return found, findable
+
+
+def range_vote_report(dev, n_batch=256, n_single=64):
+    """Point against range voting: device step time and track-finding
+    efficiency on a sample of the batch workload and of the single-event
+    workload (coarse 64-row grid), at each workload's threshold."""
+    from paper_1311_2769_gb300 import ht, synth
+    out = {}
+    for wname, n in (("batch_4096_lognormal", n_batch), ("single_event_10trk", n_single)):
+        w = synth.WORKLOADS[wname]
+        b = synth.generate(w, n_events=n)
+        hits = ht.Hits.from_batch(b, device=dev)
+        rows = {}
+        for mode, name in ((ht.HT_VOTE_POINT, "point"), (ht.HT_VOTE_RANGE, "range")):
+            ctx = ht.Context(w.grid, w.spec.layers)
+            ctx.set_option(ht.HT_OPT_VOTE_MODE, mode)
+            ctx.set_option(ht.HT_OPT_PHASE_TIMING, 1)
+            res = ht.Results(n * 200000 + 4096, n * 6000000 + 65536, device=dev)
+            ts = []
+            for it in range(4):
+                ctx.process(hits, w.threshold, w.window, res)
+                ctx.sync()
+                if it:
+                    ts.append(ctx.phase_times())
+            pk, _, hidx = res.host()
+            f, fa = track_efficiency(w.grid, b, pk)
+            rows[name] = {"ms_per_event": float(np.mean([t[2] for t in ts])) / n,
+                          "vote_ms": float(np.mean([t[0] for t in ts])),
+                          "peaks_assoc_ms": float(np.mean([t[1] for t in ts])),
+                          "peaks_per_event": len(pk) / n, "pairs_per_event": len(hidx) / n,
+                          "tracks_found": f, "tracks_findable": fa, "efficiency": f / max(fa, 1)}
+            ctx.close()
+        out[wname] = {"events": n, "threshold": w.threshold, **rows}
+    return out
 
 
 def run_reference(args):
@@ -339,6 +407,14 @@ def run_gpu(args):
         except Exception as e:  # report, do not hide, a failing loop
             serving = {"error": f"{type(e).__name__}: {e}"}
 
+    # ---- range voting against point voting (rank 0, N=1)
+    range_vote = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        try:
+            range_vote = range_vote_report(dev)
+        except Exception as e:  # report, do not hide, a failing measurement
+            range_vote = {"error": f"{type(e).__name__}: {e}"}
+
     # ---- roofline of the dominant kernel (association) and of the vote:
     # issue-bound ALU work, 6 ops per (hit, phi0, d0) cell of the method
     peaks, peak_src = _peaks()
@@ -387,6 +463,7 @@ def run_gpu(args):
         "gpu_launches": int(launches) * args.steps,
         "e2e": e2e,
         "serving": serving,
+        "range_vote": range_vote,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, batch)

@@ -136,6 +136,26 @@ typedef struct {
                                       bands; same results.  Default 3; no effect when the kappa
                                       range does not contain 0. */
 
+#define HT_OPT_VOTE_MODE 13        /* HT_VOTE_POINT (default) or HT_VOTE_RANGE */
+#define HT_OPT_ASSOC_CURSORS 14    /* association row cursors per warp, a multiple of 32 (0 = auto:
+                                      as many as fit 9 KB of shared memory per warp, 256..1024);
+                                      a column block with more peaks is walked once per block of
+                                      cursors.  Reading gives the resolved value. */
+
+/* Vote modes.  HT_VOTE_POINT: a hit votes, in each (phi0, d0) column, for the
+ * kappa bin of its curve at the column's centre (Section 3's vote, point
+ * sampled).  HT_VOTE_RANGE: a hit votes, in each (phi0, d0) cell, for every
+ * kappa bin from the lowest to the highest bin of its curve at the cell's
+ * four corners (phi0 edges m 2pi/n_phi, periodic; d0 edges d0_min +
+ * n (d0_max - d0_min)/n_d0), clipped to the kappa range, and for none when a
+ * corner is the hit's own perigee point (a non-positive denominator); it
+ * joins peak (i, j, k) when those bins reach within `window` of k.  Range
+ * voting collects every hit of an unsmeared off-centre track in the track's
+ * own cell, which point sampling misses.  Bins are defined in binary64 as for
+ * the point vote. */
+#define HT_VOTE_POINT 0
+#define HT_VOTE_RANGE 1
+
 #define HT_MODE_BATCHED 0 /* one persistent launch per kernel over all (event, tile) items */
 #define HT_MODE_PLAIN 1   /* one launch sequence per event */
 

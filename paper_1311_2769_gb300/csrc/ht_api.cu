@@ -64,6 +64,10 @@ struct ht_ctx {
     int n_layers = 0;
     KConsts K{};
     std::vector<float> h_cphi, h_sphi, h_d0;
+    std::vector<float> h_ecos, h_esin, h_de;  // range voting: phi0 and d0 edges
+    float* d_ecos = nullptr;
+    float* d_esin = nullptr;
+    float4* d_edtab = nullptr;
     float* d_cphi = nullptr;
     float* d_sphi = nullptr;
     float4* d_dtab = nullptr;
@@ -76,6 +80,8 @@ struct ht_ctx {
     int tile_phi = 0, tile_d = 0, threads = 0;
     int atile_phi = 0, atile_d = 0;  // association item (0 = auto)
     int prune = 3;                   // bit 0: vote, bit 1: association drop hits without a d0 band
+    int vote_mode = HT_VOTE_POINT;
+    int acap = 0;  // association row cursors per warp (0 = auto)
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
@@ -83,6 +89,7 @@ struct ht_ctx {
     // resolved tile configuration
     int r_tile_phi = 1, r_tile_d = 1, r_threads = 256, r_smem = 0, r_blocks_per_sm = 1;
     bool r_band = false, a_band = false;
+    int r_variant = 0;  // vote kernel: 0 full sweep, 1 band compaction, 2 range
     int a_tile_phi = 1, a_tile_d = 1, a_threads = 256, a_cap = 0, a_blocks_per_sm = 1;  // association item
     size_t a_warp_bytes = 0;
 
@@ -166,6 +173,22 @@ const double kPi = 3.14159265358979323846;
 
 // Bin-centre tables (Section 3 parameter grid): phi0_i = (i + 1/2) 2 pi / n_phi,
 // d0_j = d0_min + (j + 1/2)(d0_max - d0_min) / n_d0, rounded to float once.
+// Range voting's cell edges: phi0 edges m 2pi/n_phi (cell i spans edges i and
+// i + 1 mod n_phi) and the n_d0 + 1 d0 edges, each rounded to float once.
+void build_edges(const ht_grid& g, std::vector<float>& c, std::vector<float>& s, std::vector<float>& d) {
+    c.resize(g.n_phi);
+    s.resize(g.n_phi);
+    d.resize(g.n_d0 + 1);
+    const double dphi = 2.0 * kPi / (double)g.n_phi;
+    for (int m = 0; m < g.n_phi; ++m) {
+        const double phi = (double)m * dphi;
+        c[m] = (float)std::cos(phi);
+        s[m] = (float)std::sin(phi);
+    }
+    const double wd = ((double)g.d0_max - (double)g.d0_min) / (double)g.n_d0;
+    for (int n = 0; n <= g.n_d0; ++n) d[n] = (float)((double)g.d0_min + (double)n * wd);
+}
+
 void build_tables(const ht_grid& g, std::vector<float>& c, std::vector<float>& s, std::vector<float>& d) {
     c.resize(g.n_phi);
     s.resize(g.n_phi);
@@ -266,15 +289,19 @@ int resolve_tiles(ht_ctx* ctx) {
             }
     }
     int thr = ctx->threads > 0 ? ctx->threads : 256;
-    const bool band = (ctx->prune & 1) && ctx->K.band_ok;
-    ctx->a_band = (ctx->prune & 2) && ctx->K.band_ok;
-    const int smem = vote_smem_bytes(tp, td, nk, thr, band);
+    const bool range = ctx->vote_mode == HT_VOTE_RANGE;
+    // bands bound point votes only: range voting sweeps every cell
+    const bool band = !range && (ctx->prune & 1) && ctx->K.band_ok;
+    ctx->a_band = !range && (ctx->prune & 2) && ctx->K.band_ok;
+    const int variant = range ? 2 : (band ? 1 : 0);
+    const int smem = vote_smem_bytes(tp, td, nk, thr, variant);
     if (smem > 227 * 1024)
         return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d needs %d B of shared memory", tp, td, nk, smem);
-    CU(vote_prepare(tp, nk, smem, band));
+    CU(vote_prepare(tp, nk, smem, variant));
     int per_sm = 0;
-    CU(vote_occupancy(tp, nk, thr, smem, &per_sm, band));
+    CU(vote_occupancy(tp, nk, thr, smem, &per_sm, variant));
     ctx->r_band = band;
+    ctx->r_variant = variant;
     if (per_sm < 1) return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d with %d threads cannot launch", tp, td, nk, thr);
     ctx->r_tile_phi = tp;
     ctx->r_tile_d = td;
@@ -290,6 +317,28 @@ int resolve_tiles(ht_ctx* ctx) {
     // then as many cursors as fit, 256 to 1024.
     const int nphi = ctx->grid.n_phi;
     constexpr size_t kWarpBudget = 9216;
+    const int athr = std::min(thr, 256);
+    if (range) {
+        // range association: one row x up to 32 d0 columns per item
+        int atd = std::min(ctx->atile_d > 0 ? ctx->atile_d : 32, std::min(nd, 32));
+        while (atd > 1 && assoc_range_warp_smem(atd, nk, 256) > kWarpBudget) atd = (atd + 1) / 2;
+        const size_t fixed = assoc_range_warp_smem(atd, nk, 0);
+        int cap = fixed + 4 * 256 <= kWarpBudget ? (int)((kWarpBudget - fixed) / 4) & ~31 : 256;
+        cap = ctx->acap > 0 ? ctx->acap : std::min(cap, 1024);
+        const size_t wbytes = assoc_range_warp_smem(atd, nk, cap);
+        const int asmem = (int)(wbytes * (athr / 32));
+        if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association item does not fit shared memory");
+        int ablocks = 0;
+        CU(assoc_range_prepare(nk, asmem, athr, &ablocks));
+        if (ablocks < 1) return fail(ctx, HT_ERR_INVALID_ARG, "association kernel cannot launch");
+        ctx->a_tile_phi = 1;
+        ctx->a_tile_d = atd;
+        ctx->a_threads = athr;
+        ctx->a_cap = cap;
+        ctx->a_warp_bytes = wbytes;
+        ctx->a_blocks_per_sm = ablocks;
+        return HT_OK;
+    }
     auto fits = [&](int rows, int cols) { return assoc_warp_smem(rows, cols, nk, 256) <= kWarpBudget; };
     int atp = ctx->atile_phi, atd = ctx->atile_d;
     if (atp == 0 && atd == 0) {
@@ -316,11 +365,10 @@ int resolve_tiles(ht_ctx* ctx) {
         return fail(ctx, HT_ERR_INVALID_ARG,
                     "association item %d x %d: at most 32 columns, and more than one row needs all %d d0 columns",
                     atp, atd, nd);
-    const int athr = std::min(thr, 256);
     const bool aband = ctx->a_band;
     const size_t fixed = assoc_warp_smem(atp, atd, nk, 0);
     int cap = fixed + 4 * 256 <= kWarpBudget ? (int)((kWarpBudget - fixed) / 4) & ~31 : 256;
-    cap = std::min(cap, 1024);
+    cap = ctx->acap > 0 ? ctx->acap : std::min(cap, 1024);
     const size_t wbytes = assoc_warp_smem(atp, atd, nk, cap);
     const int asmem = (int)(wbytes * (athr / 32));
     if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association item does not fit shared memory");
@@ -423,6 +471,9 @@ VoteParams vote_params(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent)
     p.cphi = ctx->d_cphi;
     p.sphi = ctx->d_sphi;
     p.dtab = ctx->d_dtab;
+    p.ecos = ctx->d_ecos;
+    p.esin = ctx->d_esin;
+    p.edtab = ctx->d_edtab;
     p.K = ctx->K;
     p.stats = ctx->count_stages ? ctx->d_stats : nullptr;
     return p;
@@ -436,9 +487,9 @@ int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStrea
         CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
         CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), s));
         const int grid = std::min<int64_t>(p.n_items, (int64_t)ctx->sms * ctx->r_blocks_per_sm);
-        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s, ctx->r_band));
+        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s, ctx->r_variant));
     } else {
-        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_band));
+        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_variant));
     }
     return HT_OK;
 }
@@ -488,7 +539,8 @@ int run_detect_scan(ht_ctx* ctx, const PeakParams& pp, cudaStream_t s) {
 // Association of events [event0, event0 + ne) (their peaks numbered from the
 // column bases): the item-layout fields, a zeroed work counter, a grid of
 // resident blocks.
-int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, const int32_t* order,
+// pass: 0 point association, 1 range counting, 2 range writing
+int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, const int32_t* order, int pass,
                      cudaStream_t s) {
     a.x = ctx->cx;
     a.y = ctx->cy;
@@ -509,6 +561,9 @@ int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, co
     a.cphi = ctx->d_cphi;
     a.sphi = ctx->d_sphi;
     a.dtab = ctx->d_dtab;
+    a.ecos = ctx->d_ecos;
+    a.esin = ctx->d_esin;
+    a.edtab = ctx->d_edtab;
     a.K = ctx->K;
     a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
     const int64_t items = (int64_t)ne * ((ctx->grid.n_phi + ctx->a_tile_phi - 1) / ctx->a_tile_phi) *
@@ -517,7 +572,10 @@ int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, co
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>((items + warps - 1) / warps, (int64_t)ctx->sms * ctx->a_blocks_per_sm));
     CU(cudaMemsetAsync(ctx->d_aqueue, 0, sizeof(unsigned long long), s));
-    CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_threads, grid, s));
+    if (pass == 0)
+        CU(launch_assoc(a, ctx->a_tile_phi, ctx->a_threads, grid, s));
+    else
+        CU(launch_assoc_range(a, pass == 1, ctx->a_threads, grid, s));
     return HT_OK;
 }
 
@@ -527,6 +585,18 @@ int mark(ht_ctx* ctx, int which, cudaStream_t s);
 int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* order, int64_t peak_cap,
                     int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, bool timed,
                     cudaStream_t s) {
+    const bool range = ctx->vote_mode == HT_VOTE_RANGE;
+    if (range) {
+        // row lengths by a counting pass (window sums over-count range votes)
+        AssocParams c{};
+        c.peak_offsets = peak_offsets;
+        c.peak_cap = peak_cap;
+        c.window = window;
+        c.paircnt = ctx->paircnt.p;
+        c.extra_pairs = ctx->d_scal + 4;
+        const int st = launch_assoc_ctx(ctx, c, event0, ne, order, 1, s);
+        if (st) return st;
+    }
     CU(cudaMemcpyAsync(ctx->d_scal + 3, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     ScanRange r{};
     r.in = ctx->paircnt.p;
@@ -548,7 +618,7 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* orde
         const int st = mark(ctx, 4, s);
         if (st) return st;
     }
-    return launch_assoc_ctx(ctx, a, event0, ne, order, s);
+    return launch_assoc_ctx(ctx, a, event0, ne, order, range ? 2 : 0, s);
 }
 
 // The legacy default stream cannot be captured into a graph; a caller's NULL
@@ -593,7 +663,8 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
         st = run_vote(ctx, e0, ne, !plain, s);
         if (st) return st;
         if (single && (st = mark(ctx, 1, s))) return st;
-        PeakParams pp = peak_params(ctx, e0, ne, thr, peaks, peak_cap, window);
+        // range voting counts rows in the association (window sums over-count)
+        PeakParams pp = peak_params(ctx, e0, ne, thr, peaks, peak_cap, ctx->vote_mode == HT_VOTE_RANGE ? -1 : window);
         st = run_detect_scan(ctx, pp, s);
         if (st) return st;
         CU(launch_emit(pp, s));
@@ -601,7 +672,7 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
                              window, single, s);
         if (st) return st;
         if (single && (st = mark(ctx, 2, s))) return st;
-        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1;
+        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode == HT_VOTE_RANGE ? 1 : 0);
     }
     if (single && (st = mark(ctx, 3, s))) return st;
     if (ctx->c_events == 0 && peak_offsets && peak_cap >= 0)
@@ -672,6 +743,12 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
         // (d0, 2 d0, d0^2, d0 * S2): the last is the kappa-scaled d0 of stage 1
         dt[j] = make_float4(d, d + d, d * d, (float)((double)d * (double)ctx->K.S2));
     }
+    build_edges(*grid, ctx->h_ecos, ctx->h_esin, ctx->h_de);
+    std::vector<float4> dte(grid->n_d0 + 1);
+    for (int n = 0; n <= grid->n_d0; ++n) {
+        const float d = ctx->h_de[n];
+        dte[n] = make_float4(d, d + d, d * d, (float)((double)d * (double)ctx->K.S2));
+    }
     int st = HT_OK;
     auto bad = [&](cudaError_t e) {
         if (e == cudaSuccess) return false;
@@ -681,12 +758,18 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
     if (bad(cudaMalloc(&ctx->d_cphi, grid->n_phi * sizeof(float))) ||
         bad(cudaMalloc(&ctx->d_sphi, grid->n_phi * sizeof(float))) ||
         bad(cudaMalloc(&ctx->d_dtab, grid->n_d0 * sizeof(float4))) ||
+        bad(cudaMalloc(&ctx->d_ecos, grid->n_phi * sizeof(float))) ||
+        bad(cudaMalloc(&ctx->d_esin, grid->n_phi * sizeof(float))) ||
+        bad(cudaMalloc(&ctx->d_edtab, (grid->n_d0 + 1) * sizeof(float4))) ||
         bad(cudaMalloc(&ctx->d_scal, 8 * sizeof(int64_t))) || bad(cudaMalloc(&ctx->d_err, sizeof(int32_t))) ||
         bad(cudaMalloc(&ctx->d_queue, 16)) || bad(cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long))) ||
         bad(cudaMallocHost(&ctx->h_pinned, 8 * sizeof(int64_t))) ||
         bad(cudaMemcpy(ctx->d_cphi, ctx->h_cphi.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
         bad(cudaMemcpy(ctx->d_sphi, ctx->h_sphi.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
         bad(cudaMemcpy(ctx->d_dtab, dt.data(), grid->n_d0 * sizeof(float4), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemcpy(ctx->d_ecos, ctx->h_ecos.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemcpy(ctx->d_esin, ctx->h_esin.data(), grid->n_phi * sizeof(float), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemcpy(ctx->d_edtab, dte.data(), (grid->n_d0 + 1) * sizeof(float4), cudaMemcpyHostToDevice)) ||
         bad(cudaMemset(ctx->d_err, 0, sizeof(int32_t))) || bad(cudaMemset(ctx->d_stats, 0, 4 * sizeof(unsigned long long))) ||
         bad(cudaMemset(ctx->d_scal, 0, 8 * sizeof(int64_t)))) {
         ht_destroy(ctx);
@@ -714,6 +797,8 @@ int ht_destroy(ht_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     for (auto& e : ctx->tev)
         if (e) cudaEventDestroy(e);
+    for (void* p : {(void*)ctx->d_ecos, (void*)ctx->d_esin, (void*)ctx->d_edtab})
+        if (p) cudaFree(p);
     for (void* p : {(void*)ctx->d_cphi, (void*)ctx->d_sphi, (void*)ctx->d_dtab, (void*)ctx->d_scal, (void*)ctx->d_err,
                     (void*)ctx->d_queue, (void*)ctx->d_stats})
         if (p) cudaFree(p);
@@ -778,6 +863,17 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             if (value < 0 || value > ctx->grid.n_d0) return fail(ctx, HT_ERR_INVALID_ARG, "association tile_d0 out of range");
             ctx->atile_d = (int)value;
             break;
+        case HT_OPT_ASSOC_CURSORS:
+            if (value < 0 || value > 65536 || (value % 32) != 0)
+                return fail(ctx, HT_ERR_INVALID_ARG, "association cursors must be 0 or a multiple of 32 up to 65536");
+            ctx->acap = (int)value;
+            break;
+        case HT_OPT_VOTE_MODE:
+            if (value != HT_VOTE_POINT && value != HT_VOTE_RANGE)
+                return fail(ctx, HT_ERR_INVALID_ARG, "vote mode must be HT_VOTE_POINT or HT_VOTE_RANGE");
+            ctx->vote_mode = (int)value;
+            ctx->have_peaks = false;
+            break;
         case HT_OPT_PHASE_TIMING:
             if (value && !ctx->tev[0])
                 for (auto& e : ctx->tev) CU(cudaEventCreate(&e));
@@ -787,7 +883,7 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
     }
     ctx->gvalid = false;
     if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS || key == HT_OPT_ATILE_PHI ||
-        key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE) {
+        key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE || key == HT_OPT_VOTE_MODE || key == HT_OPT_ASSOC_CURSORS) {
         int st = resolve_tiles(ctx);
         if (st) return st;
     }
@@ -808,6 +904,8 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_ATILE_PHI: *value = ctx->a_tile_phi; break;
         case HT_OPT_PRUNE: *value = (ctx->r_band ? 1 : 0) | (ctx->a_band ? 2 : 0); break;
         case HT_OPT_ATILE_D0: *value = ctx->a_tile_d; break;
+        case HT_OPT_VOTE_MODE: *value = ctx->vote_mode; break;
+        case HT_OPT_ASSOC_CURSORS: *value = ctx->a_cap; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
@@ -832,7 +930,7 @@ int ht_vote(ht_ctx* ctx, const ht_hits* hits, void* stream) {
         for (int32_t e = 0; e < ctx->c_events; ++e) {
             VoteParams p = vote_params(ctx, e, 1, false);
             p.acc = ctx->acc.p + (int64_t)e * ctx->cells;
-            CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_band));
+            CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_variant));
         }
     } else {
         st = run_vote(ctx, 0, ctx->c_events, true, s);
@@ -884,8 +982,19 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     CU(cudaMemsetAsync(ctx->d_scal, 0, 8 * sizeof(int64_t), s));
     ctx->h_pinned[0] = np;
     CU(cudaMemcpyAsync(ctx->d_scal + 0, ctx->h_pinned, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    PeakParams pp = peak_params(ctx, 0, ctx->c_events, ctx->last_threshold, ctx->peaks.p, np, window);
-    CU(launch_paircount(pp, ctx->d_scal + 2, ctx->d_scal + 0, s));
+    if (ctx->vote_mode == HT_VOTE_RANGE) {
+        AssocParams c{};
+        c.peak_offsets = ctx->peakoff.p;
+        c.peak_cap = np;
+        c.window = window;
+        c.paircnt = ctx->paircnt.p;
+        c.extra_pairs = ctx->d_scal + 4;
+        const int st = launch_assoc_ctx(ctx, c, 0, ctx->c_events, nullptr, 1, s);
+        if (st) return st;
+    } else {
+        PeakParams pp = peak_params(ctx, 0, ctx->c_events, ctx->last_threshold, ctx->peaks.p, np, window);
+        CU(launch_paircount(pp, ctx->d_scal + 2, ctx->d_scal + 0, s));
+    }
     CU(cudaMemcpyAsync(ctx->d_scal + 3, ctx->d_scal + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     ScanRange r{};
     r.in = ctx->paircnt.p;
@@ -907,7 +1016,7 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     a.hit_idx = ctx->hitidx.p;
     a.pair_cap = total;
     a.window = window;
-    const int st = launch_assoc_ctx(ctx, a, 0, ctx->c_events, nullptr, s);
+    const int st = launch_assoc_ctx(ctx, a, 0, ctx->c_events, nullptr, ctx->vote_mode == HT_VOTE_RANGE ? 2 : 0, s);
     if (st) return st;
     CU(cudaMemcpyAsync(peak_offsets, ctx->peakoff.p, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     const int64_t ncopy = std::min(total, cap);
@@ -971,7 +1080,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         key.vals[9] = ctx->r_threads;
         key.vals[10] = ctx->count_stages * 2 + ctx->timing;
         key.vals[11] = ((int64_t)ctx->a_tile_phi << 40) | ((int64_t)ctx->a_tile_d << 20) | ((int64_t)ctx->a_cap << 2) |
-                       (ctx->r_band ? 2 : 0) | (ctx->a_band ? 1 : 0);
+                       (ctx->r_band ? 2 : 0) | (ctx->a_band ? 1 : 0) | ((int64_t)ctx->vote_mode << 60);
         if (!ctx->gvalid || !(key == ctx->gkey)) {
             if (ctx->gexec) {
                 cudaGraphExecDestroy(ctx->gexec);
@@ -1108,7 +1217,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     for (int tp : {1, 2, 4, 8}) {
         if (tp > ctx->grid.n_phi) continue;
         for (int td : tds) {
-            const int smem = vote_smem_bytes(tp, td, nk, 256, (ctx->prune & 1) && ctx->K.band_ok);
+            const int smem = vote_smem_bytes(tp, td, nk, 256, ctx->r_variant);
             if (smem > 200 * 1024 || smem < 8 * 1024) continue;
             for (int thr : {128, 256}) {
                 ctx->tile_phi = tp;

@@ -25,6 +25,9 @@ struct VoteParams {
     const float* cphi;
     const float* sphi;
     const float4* dtab;    // (d0_j, 2 d0_j, d0_j^2, d0_j * S2)
+    const float* ecos;     // range voting: cos/sin of the phi0 edges m 2pi/n_phi
+    const float* esin;
+    const float4* edtab;   // range voting: the n_d0 + 1 d0 edges, as dtab
     KConsts K;
     unsigned long long* stats;
 };
@@ -68,6 +71,11 @@ struct AssocParams {
     size_t warp_bytes;      // shared memory per warp
     const int32_t* order;   // wave-local event order (largest first) or nullptr
     unsigned long long* queue;  // work counter, zeroed before the launch
+    const float* ecos;      // range association: phi0 edges and d0 edges
+    const float* esin;
+    const float4* edtab;
+    int32_t* paircnt;       // range counting pass: row lengths of stored peaks
+    int64_t* extra_pairs;   // range counting pass: pairs of peaks past the cap (device scalar)
     const float* cphi;
     const float* sphi;
     const float4* dtab;
@@ -92,12 +100,13 @@ struct ScanRange {
 constexpr int kScanBlocks = 304;
 constexpr int kScanThreads = 1024;
 
-int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band);
-cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes, bool band);
-cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, bool band);
+// vote kernel variants: 0 full sweep, 1 d0-band compaction, 2 range voting
+int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant);
+cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes, int variant);
+cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant);
 cudaError_t launch_finalize(int64_t* scal, cudaStream_t s);
 cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s,
-                        bool band);
+                        int variant);
 cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer, int64_t n_hits,
                             const int32_t* offs, int32_t n_events, int32_t n_layers, int32_t* err,
                             cudaStream_t s);
@@ -113,6 +122,9 @@ cudaError_t launch_scan(const ScanRange& r, int64_t* scratch /* 2 * kScanBlocks 
 size_t assoc_warp_smem(int rows, int wd, int nk, int cap);
 cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band, int threads, int* blocks_per_sm);
 cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int grid, cudaStream_t s);
+size_t assoc_range_warp_smem(int wd, int nk, int cap);
+cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm);
+cudaError_t launch_assoc_range(const AssocParams& p, bool count, int threads, int grid, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
 
 }  // namespace ht

@@ -283,4 +283,114 @@ __device__ __forceinline__ float q_of(float x, float y, float c, float s) {
     return fmaf(y, c, -__fmul_rn(x, s));
 }
 
+
+// ---- corner codes (range voting) -----------------------------------------
+// A range vote bins the curve at a cell's four corners.  A corner's code is
+// kCodeUndef when its denominator is not positive (binary64), -1 below the
+// kappa range, n_kappa above it, else the bin; kCodeUndecided marks a stage
+// that could not decide.
+constexpr int kCodeUndef = -2, kCodeUndecided = -3;
+
+__device__ __forceinline__ int clamp_code(int v, int nk) { return v < 0 ? -1 : (v > nk ? nk : v); }
+
+// Stage 1 for a corner: decided when den > den_min (so the bound holds) and
+// both ends of [w - tau, w + tau] give the same code; far outside the kappa
+// range that holds even when an end lies near an integer.
+__device__ __forceinline__ int code_stage1(const S1& o, float dmin, int nk) {
+    const int a = clamp_code((int)o.kb, nk);
+    const int b = clamp_code((int)(__float_as_uint(o.fhi) - 0x4B400000u), nk);
+    return (o.den > dmin && a == b) ? a : kCodeUndecided;
+}
+
+// Stage 2 for a corner (the double-float evaluation of cell_dd).
+__device__ __forceinline__ int code_dd(float x, float y, float c, float s, float d, float R1, const KConsts& K) {
+    float p1, e1, p2, e2;
+    two_prod(y, c, p1, e1);
+    two_prod(x, s, p2, e2);
+    float s1, t1;
+    two_sum(p1, -p2, s1, t1);
+    float qh, ql;
+    two_sum(s1, __fadd_rn(t1, __fsub_rn(e1, e2)), qh, ql);
+    float s2, t2;
+    two_sum(qh, -d, s2, t2);
+    float ah, al;
+    two_sum(s2, __fadd_rn(t2, ql), ah, al);
+    float xx, exx, yy, eyy, dd, edd;
+    two_prod(x, x, xx, exx);
+    two_prod(y, y, yy, eyy);
+    two_prod(d, d, dd, edd);
+    const float d2 = __fadd_rn(d, d);
+    float mh, me;
+    two_prod(d2, qh, mh, me);
+    me = fmaf(d2, ql, me);
+    float s3, t3, s4, t4, s5, t5;
+    two_sum(xx, yy, s3, t3);
+    two_sum(s3, dd, s4, t4);
+    two_sum(s4, -mh, s5, t5);
+    const float low = __fadd_rn(__fadd_rn(__fadd_rn(exx, eyy), __fsub_rn(edd, me)),
+                                __fadd_rn(__fadd_rn(t3, t4), t5));
+    float denh, denl;
+    two_sum(s5, low, denh, denl);
+    if (!(denh > K.cDb * R1 * R1)) return kCodeUndecided;
+    const float rc = rcp_approx(denh);
+    const float q1 = __fmul_rn(ah, rc);
+    float pp, pe;
+    two_prod(q1, denh, pp, pe);
+    const float rem = fmaf(-q1, denl, __fadd_rn(__fsub_rn(__fsub_rn(ah, pp), pe), al));
+    const float q2 = __fmul_rn(rem, rc);
+    float vh, ve;
+    two_prod(q1, K.S2hi, vh, ve);
+    ve = fmaf(q1, K.S2lo, ve);
+    ve = fmaf(q2, K.S2hi, ve);
+    float s6, t6;
+    two_sum(vh, K.Hhi, s6, t6);
+    float wh, wl;
+    two_sum(s6, __fadd_rn(__fadd_rn(t6, ve), K.Hlo), wh, wl);
+    // |w - (wh + wl)| is far below one bin: two bins out is out for sure
+    if (!(wh > -2.0f)) return -1;
+    if (!(wh < (float)K.nk + 2.0f)) return K.nk;
+    const float tau2 = fmaf(fmaf(K.cGb1 * R1, R1, K.cGb2 * R1), rc, K.T0b);
+    float kf = floorf(wh);
+    float a0, b0, a1, b1;
+    two_sum(wh, -kf, a0, b0);
+    float dist_lo = __fadd_rn(a0, __fadd_rn(b0, wl));
+    two_sum(__fadd_rn(kf, 1.0f), -wh, a1, b1);
+    float dist_hi = __fadd_rn(a1, __fsub_rn(b1, wl));
+    if (dist_lo < 0.0f) {
+        kf = __fsub_rn(kf, 1.0f);
+        dist_hi = -dist_lo;
+        dist_lo = __fadd_rn(dist_lo, 1.0f);
+    }
+    const int kc = clamp_code((int)kf, K.nk);
+    if (dist_lo <= tau2 && clamp_code((int)kf - 1, K.nk) != kc) return kCodeUndecided;
+    if (dist_hi <= tau2 && clamp_code((int)kf + 1, K.nk) != kc) return kCodeUndecided;
+    return kc;
+}
+
+// Stage 3 for a corner: the binary64 definition.
+__device__ __forceinline__ int code_f64(float xf, float yf, float cf, float sf, float df, const KConsts& K) {
+    const double x = xf, y = yf, c = cf, s = sf, d = df;
+    const double q = __dsub_rn(__dmul_rn(y, c), __dmul_rn(x, s));
+    const double a = __dsub_rn(q, d);
+    const double den = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(d, d)),
+                                 __dmul_rn(__dmul_rn(2.0, d), q));
+    if (!(den > 0.0)) return kCodeUndef;
+    const double kappa = __ddiv_rn(__dmul_rn(2.0, a), den);
+    const double w = __dmul_rn(__dsub_rn(kappa, K.kmin), K.scale);
+    if (w < 0.0) return -1;
+    if (w >= (double)K.nk) return K.nk;
+    return (int)w;
+}
+
+static __device__ __noinline__ int code_slow(float x, float y, float c, float s, float d, float R1,
+                                             const KConsts& K, unsigned long long* stats) {
+    const int k = code_dd(x, y, c, s, d, R1, K);
+    if (k != kCodeUndecided) {
+        if (stats) atomicAdd(&stats[1], 1ull);
+        return k;
+    }
+    if (stats) atomicAdd(&stats[2], 1ull);
+    return code_f64(x, y, c, s, d, K);
+}
+
 }  // namespace ht

@@ -320,6 +320,156 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// range vote: every kappa bin between a cell's corner bins
+// ---------------------------------------------------------------------------
+// The tile's corners are its SPHI + 1 phi0 edges by nj + 1 d0 edges.  Each
+// thread sweeps its hit across the d0 edges, binning the SPHI + 1 corners of
+// one edge (stage 1, stages 2 and 3 for undecided corners) while keeping the
+// previous edge's codes, and votes each cell between the two edges for the
+// bins from its lowest to its highest corner code.  A vote for bins [lo, hi]
+// adds 1 at lo and subtracts 1 at hi + 1 of the column in shared memory (two
+// atomics whatever the width: an inner-layer hit can span tens of bins); the
+// flush turns each column into counts by a prefix sum over kappa.
+template <int SPHI, int NK, bool TAIL>
+__device__ __forceinline__ void vote_range_one_hit(const VoteParams& p, const float* ce, const float* se,
+                                                   const float4* dte_s, uint32_t* acc_s, int nj, int nk, int64_t h,
+                                                   bool valid) {
+    const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
+    const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
+    const HitFast hf = hit_fast(x, y, p.K);
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    float qe[SPHI + 1], qse[SPHI + 1];
+#pragma unroll
+    for (int m = 0; m <= SPHI; ++m) {
+        qe[m] = q_of(x, y, ce[m], se[m]);
+        qse[m] = qe[m] * S2;
+    }
+    int prev[SPHI + 1], cur[SPHI + 1];
+    const int col_words = SPHI * nk;
+    for (int n = 0; n <= nj; ++n) {
+        const float4 dt = dte_s[n];
+        const float Rj = hf.r2 + dt.z;
+        bool und = false;
+#pragma unroll
+        for (int m = 0; m <= SPHI; ++m) {
+            const S1 o = stage1_fast(qse[m], qe[m], dt, Rj, hf.G, H, T0);
+            cur[m] = (!TAIL || valid) ? code_stage1(o, hf.dmin, nk) : kCodeUndef;
+            und |= cur[m] == kCodeUndecided;
+        }
+        if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+            for (int m = 0; m <= SPHI; ++m)
+                if (cur[m] == kCodeUndecided) cur[m] = code_slow(x, y, ce[m], se[m], dt.x, hf.R1, p.K, p.stats);
+        }
+        if (n > 0) {
+            uint32_t* col = acc_s + (n - 1) * col_words;
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                const int a = min(min(prev[r], prev[r + 1]), min(cur[r], cur[r + 1]));
+                const int b = max(max(prev[r], prev[r + 1]), max(cur[r], cur[r + 1]));
+                const bool undef = prev[r] == kCodeUndef || prev[r + 1] == kCodeUndef || cur[r] == kCodeUndef ||
+                                   cur[r + 1] == kCodeUndef;
+                if (!undef && b >= 0 && a < nk) {
+                    const int lo = max(a, 0), hi = min(b, nk - 1);
+                    atomicAdd(col + r * nk + lo, 1u);
+                    if (hi + 1 < nk) atomicAdd(col + r * nk + hi + 1, 0xFFFFFFFFu);  // -1 mod 2^32
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m <= SPHI; ++m) prev[m] = cur[m];
+    }
+}
+
+template <int SPHI, int NK>
+__global__ void __launch_bounds__(256, 3) vote_range_kernel(const VoteParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* dte_s = reinterpret_cast<float4*>(smem_raw);
+    uint32_t* acc_s = reinterpret_cast<uint32_t*>(smem_raw + 16 * (p.tile_d + 1));
+    __shared__ int s_item;
+
+    const int nk = NK ? NK : p.K.nk;
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int tiles = p.tiles_phi * p.tiles_d;
+    const int col_words = SPHI * nk;
+
+    for (int it = 0;; ++it) {
+        int item;
+        if (p.queue) {
+            if (tid == 0) s_item = atomicAdd(p.queue, 1);
+            __syncthreads();
+            item = s_item;
+        } else {
+            if (it > 0) break;
+            item = p.item0 + blockIdx.x;
+        }
+        if (item >= p.n_items) break;
+        const int el = item / tiles;
+        const int t = item - el * tiles;
+        const int e = p.order ? p.order[el] : el;
+        const int tp = t / p.tiles_d;
+        const int td = t - tp * p.tiles_d;
+        const int i0 = tp * SPHI;
+        const int j0 = td * p.tile_d;
+        const int nj = min(p.tile_d, p.K.nd - j0);
+        const int nrows = min(SPHI, p.K.nphi - i0);
+        const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
+        const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
+
+        for (int w = tid; w < nj * col_words; w += nthr) acc_s[w] = 0u;
+        for (int n = tid; n <= nj; n += nthr) dte_s[n] = p.edtab[j0 + n];
+        // phi0 edges of the tile (periodic); rows past a ragged edge vote into
+        // tile slots that are never flushed
+        float ce[SPHI + 1], se[SPHI + 1];
+#pragma unroll
+        for (int m = 0; m <= SPHI; ++m) {
+            const int i = (i0 + m) % p.K.nphi;
+            ce[m] = p.ecos[i];
+            se[m] = p.esin[i];
+        }
+        if (p.stats && tid == 0) atomicAdd(&p.stats[0], (unsigned long long)((he - hb) * nrows * nj));
+        __syncthreads();
+
+        const int64_t nfull = ((he - hb) / nthr) * nthr;
+        for (int64_t h = hb + tid; h < hb + nfull; h += nthr)
+            vote_range_one_hit<SPHI, NK, false>(p, ce, se, dte_s, acc_s, nj, nk, h, true);
+        {
+            const int64_t h = hb + nfull + tid;
+            if (hb + nfull + (tid - lane) < he)
+                vote_range_one_hit<SPHI, NK, true>(p, ce, se, dte_s, acc_s, nj, nk, h, h < he);
+        }
+        __syncthreads();
+
+        // counts = prefix sums of the differences along kappa, 32 bins a step
+        uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
+        const int warp = tid >> 5, nw = nthr >> 5;
+        const int nrj = nrows * nj;
+        for (int row = warp; row < nrj; row += nw) {
+            const int r = row / nj;
+            const int j = row - r * nj;
+            const uint32_t* src = acc_s + j * col_words + r * nk;
+            uint32_t* dst = dst_e + ((int64_t)(i0 + r) * p.K.nd + (j0 + j)) * nk;
+            uint32_t carry = 0;
+            for (int k0 = 0; k0 < nk; k0 += 32) {
+                const int kk = k0 + lane;
+                uint32_t v = kk < nk ? src[kk] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                v += carry;
+                if (kk < nk) dst[kk] = v;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // input validation (device-resident batches)
 // bit 1: non-finite or |coordinate| > 1e4; bit 2: layer out of range; bit 4: offsets
 // ---------------------------------------------------------------------------
@@ -1032,6 +1182,217 @@ __global__ void __launch_bounds__(256, 3) assoc_kernel(const AssocParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// range association: one warp per item (one phi0 row x up to wd d0 columns),
+// hits 32 at a time in increasing order
+// ---------------------------------------------------------------------------
+// For every column that holds a peak, each lane forms its hit's range from
+// the cell's four corner codes (the d0 edge shared with the previous column
+// is kept); when some lane's range reaches a bin within `window` of a peak,
+// every peak of the column in reach takes the qualifying lanes at its row
+// cursor by ballot rank.  Rows thus come out in hit order.  The counting
+// instance only moves the cursors and leaves each peak's row length (the
+// hits whose range reaches it, which the window sums of a range-voted
+// accumulator over-count) in paircnt, or in extra_pairs past the peak cap;
+// the writing instance then fills the rows the scan of those counts opened.
+struct RangeWarp {
+    float4* dte;     // [wd + 1] d0 edges of the item
+    uint32_t* cur;   // [cap] row cursors (COUNT: counts) of the pass's peaks
+    uint32_t* mask;  // [wd][nkw] peak bits
+    int32_t* lpre;   // [wd][nkw] item-local id of the first peak of each word
+    uint32_t* nearb; // [wd][nkw] bins within `window` of a peak
+};
+
+__host__ __device__ inline size_t assoc_range_warp_bytes(int wd, int nk, int cap) {
+    const size_t nkw = (nk + 31) / 32;
+    return (16 * (size_t)(wd + 1) + 4 * (size_t)cap + 12 * (size_t)wd * nkw + 15) & ~size_t(15);
+}
+
+// Corner codes of the item's two phi0 edges at d0 edge n.
+__device__ __forceinline__ void range_edge_codes(const AssocParams& p, float x, float y, const HitFast& hf,
+                                                 const float* qe, const float* qse, const float* ce, const float* se,
+                                                 float4 dt, bool valid, int nk, int* code) {
+    const float Rj = hf.r2 + dt.z;
+    bool und = false;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const S1 o = stage1_fast(qse[m], qe[m], dt, Rj, hf.G, p.K.H, p.K.T0);
+        code[m] = valid ? code_stage1(o, hf.dmin, nk) : kCodeUndef;
+        und |= code[m] == kCodeUndecided;
+    }
+    if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+            if (code[m] == kCodeUndecided) code[m] = code_slow(x, y, ce[m], se[m], dt.x, hf.R1, p.K, p.stats);
+    }
+}
+
+template <int NK, bool COUNT>
+__global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = NK ? NK : p.K.nk;
+    const int nkw = (nk + 31) >> 5;
+    const int WD = p.wd;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RangeWarp S;
+    {
+        unsigned char* ptr = smem_raw + (size_t)warp * p.warp_bytes;
+        S.dte = reinterpret_cast<float4*>(ptr);
+        ptr += 16 * (WD + 1);
+        S.cur = reinterpret_cast<uint32_t*>(ptr);
+        ptr += 4 * p.cap;
+        S.mask = reinterpret_cast<uint32_t*>(ptr);
+        S.lpre = reinterpret_cast<int32_t*>(S.mask + WD * nkw);
+        S.nearb = reinterpret_cast<uint32_t*>(S.lpre + WD * nkw);
+    }
+    const int tiles_d = (p.K.nd + WD - 1) / WD;
+    const int64_t tiles = (int64_t)p.K.nphi * tiles_d;
+    const int64_t n_items = (int64_t)p.n_events * tiles;
+    const unsigned lt = lanemask_lt();
+    const float S2 = p.K.S2;
+    const int w = p.window;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(p.queue, 1ull);
+        const int64_t item = (int64_t)__shfl_sync(0xffffffffu, it, 0);
+        if (item >= n_items) break;
+        const int el = (int)(item / tiles);
+        const int64_t t = item - (int64_t)el * tiles;
+        const int e = p.order ? p.order[el] : el;
+        const int i0 = (int)(t / tiles_d), td = (int)(t - (int64_t)i0 * tiles_d);
+        const int j0 = td * WD;
+        const int nj = min(WD, p.K.nd - j0);
+        const int64_t colA = ((int64_t)e * p.K.nphi + i0) * p.K.nd + j0;
+        const bool live = lane < nj;
+        const int n = live ? p.npk[colA + lane] : 0;
+        const int64_t cb = live ? p.colbase[colA + lane] : 0;
+        const int64_t P0 = __shfl_sync(0xffffffffu, cb, 0);
+        const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)n);
+        // counting takes every peak (those past the cap add to extra_pairs);
+        // writing only the stored ones (id < peak_cap)
+        const int npk = COUNT ? tot : (int)clamp64(p.peak_cap - P0, 0, tot);
+        if (npk == 0) continue;
+        const int lo_c = (int)(cb - P0), hi_c = lo_c + n;
+        __syncwarp();  // the previous item's tables are no longer read
+        for (int v = lane; v < WD * nkw; v += 32) {
+            const int c = v / nkw, wd = v - (v / nkw) * nkw;
+            const bool ok = c < nj;
+            const int64_t col = colA + c;
+            S.mask[v] = ok ? p.mask[col * nkw + wd] : 0u;
+            S.lpre[v] = ok ? (int)(p.colbase[col] - P0) + p.wpre[col * nkw + wd] : 0;
+        }
+        for (int v = lane; v <= nj; v += 32) S.dte[v] = p.edtab[j0 + v];
+        __syncwarp();
+        for (int v = lane; v < WD * nkw; v += 32) {
+            const int wd = v - (v / nkw) * nkw;
+            const uint32_t* m = S.mask + (v - wd);
+            uint32_t nb = m[wd];
+            const uint32_t hi_w = wd + 1 < nkw ? m[wd + 1] : 0u, lo_w = wd > 0 ? m[wd - 1] : 0u;
+            for (int o = 1; o <= w; ++o) nb |= (m[wd] >> o) | (hi_w << (32 - o)) | (m[wd] << o) | (lo_w >> (32 - o));
+            S.nearb[v] = nb;
+        }
+        const int i1 = (i0 + 1) % p.K.nphi;
+        const float ce[2] = {p.ecos[i0], p.ecos[i1]}, se[2] = {p.esin[i0], p.esin[i1]};
+        const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
+        const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
+        const int64_t eh = he - hb > 1 ? he - hb : 1;
+        const int step = COUNT ? p.cap : (int)clamp64(0xFFFFFFFFll / eh, 1, p.cap);
+        for (int L0 = 0; L0 < npk; L0 += step) {
+            const int L1 = min(npk, L0 + step);
+            const int64_t Q = COUNT ? 0 : p.peak_offsets[P0 + L0];
+            __syncwarp();
+            for (int l = lane; l < L1 - L0; l += 32)
+                S.cur[l] = COUNT ? 0u : (uint32_t)(p.peak_offsets[P0 + L0 + l] - Q);
+            const unsigned jmask = __ballot_sync(0xffffffffu, live && hi_c > L0 && lo_c < L1);
+            __syncwarp();
+            for (int64_t h0 = hb; h0 < he; h0 += 32) {
+                const int64_t hh = h0 + lane;
+                const bool valid = hh < he;
+                const float x = valid ? p.x[hh] : 0.0f;
+                const float y = valid ? p.y[hh] : 0.0f;
+                const HitFast hf = hit_fast(x, y, p.K);
+                float qe[2], qse[2];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    qe[m] = q_of(x, y, ce[m], se[m]);
+                    qse[m] = qe[m] * S2;
+                }
+                int left[2], right[2];
+                int ln = -2;  // d0 edge whose codes are in `right`
+                unsigned jm = jmask;
+                while (jm) {
+                    const int j = __ffs(jm) - 1;
+                    jm &= jm - 1u;
+                    if (j == ln) {
+                        left[0] = right[0];
+                        left[1] = right[1];
+                    } else {
+                        range_edge_codes(p, x, y, hf, qe, qse, ce, se, S.dte[j], valid, nk, left);
+                    }
+                    range_edge_codes(p, x, y, hf, qe, qse, ce, se, S.dte[j + 1], valid, nk, right);
+                    ln = j + 1;
+                    const int a = min(min(left[0], left[1]), min(right[0], right[1]));
+                    const int b = max(max(left[0], left[1]), max(right[0], right[1]));
+                    const bool def = left[0] != kCodeUndef && left[1] != kCodeUndef && right[0] != kCodeUndef &&
+                                     right[1] != kCodeUndef && b >= 0 && a < nk;
+                    const int lo = max(a, 0), hi = min(b, nk - 1);
+                    // near-peak bins inside [lo, hi]
+                    bool cand = false;
+                    if (def) {
+                        const uint32_t* nb = S.nearb + j * nkw;
+                        for (int wd = lo >> 5; wd <= (hi >> 5); ++wd) {
+                            uint32_t bits = nb[wd];
+                            if (wd == (lo >> 5)) bits &= ~0u << (lo & 31);
+                            if (wd == (hi >> 5)) bits &= ~0u >> (31 - (hi & 31));
+                            cand |= bits != 0u;
+                        }
+                    }
+                    if (!__any_sync(0xffffffffu, cand)) continue;
+                    const int kmin = __reduce_min_sync(0xffffffffu, cand ? lo : 0x7fffffff);
+                    const int kmax = __reduce_max_sync(0xffffffffu, cand ? hi : -1);
+                    const int plo = max(kmin - w, 0), phi = min(kmax + w, nk - 1);
+                    const uint32_t* mw = S.mask + j * nkw;
+                    const int32_t* lp = S.lpre + j * nkw;
+                    for (int wd = plo >> 5; wd <= (phi >> 5); ++wd) {
+                        const uint32_t full = mw[wd];
+                        uint32_t bits = full;
+                        if (wd == (plo >> 5)) bits &= ~0u << (plo & 31);
+                        if (wd == (phi >> 5)) bits &= ~0u >> (31 - (phi & 31));
+                        while (bits) {
+                            const int bt = __ffs(bits) - 1;
+                            bits &= bits - 1u;
+                            const int local = lp[wd] + __popc(full & ((1u << bt) - 1u));
+                            if (local < L0 || local >= L1) continue;
+                            const int kp = (wd << 5) + bt;
+                            const bool sel = cand && lo <= kp + w && hi >= kp - w;
+                            const unsigned bb = __ballot_sync(0xffffffffu, sel);
+                            if (!bb) continue;
+                            uint32_t v = 0;
+                            if (lane == 0) v = S.cur[local - L0];  // only lane 0 moves cursors
+                            const uint32_t base = __shfl_sync(0xffffffffu, v, 0);
+                            if (!COUNT && sel) {
+                                const int64_t pos = Q + (int64_t)base + __popc(bb & lt);
+                                if (pos < p.pair_cap) p.hit_idx[pos] = (int32_t)hh;
+                            }
+                            if (lane == 0) S.cur[local - L0] = base + (uint32_t)__popc(bb);
+                        }
+                    }
+                }
+            }
+            if (COUNT) {
+                __syncwarp();
+                for (int l = lane; l < L1 - L0; l += 32) {
+                    const int64_t pid = P0 + L0 + l;
+                    if (pid < p.peak_cap)
+                        p.paircnt[pid] = (int32_t)S.cur[l];
+                    else if (S.cur[l])
+                        atomicAdd(reinterpret_cast<unsigned long long*>(p.extra_pairs), (unsigned long long)S.cur[l]);
+                }
+            }
+        }
+    }
+}
+
 // counts[0..1] = {peaks, pairs of stored peaks + pairs of peaks beyond the cap}
 __global__ void finalize_kernel(int64_t* scal) {
     scal[6] = scal[0];
@@ -1059,9 +1420,10 @@ __global__ void rcp_check_kernel(uint32_t first_bits, uint32_t count, unsigned l
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, bool band) {
-    const int queues = band ? (threads / 32) * kHitQueue * 8 : 0;
-    return 16 * tile_d + queues + 4 * tile_phi * tile_d * nk;
+int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant) {
+    const int queues = variant == 1 ? (threads / 32) * kHitQueue * 8 : 0;
+    const int table = variant == 2 ? 16 * (tile_d + 1) : 16 * tile_d;
+    return table + queues + 4 * tile_phi * tile_d * nk;
 }
 
 
@@ -1098,6 +1460,30 @@ static void* vote_band_instance(int tile_phi, int nk) {
     return nullptr;
 }
 
+template <int S, int N>
+static void* vote_range_fn() {
+    return reinterpret_cast<void*>(vote_range_kernel<S, N>);
+}
+
+static void* vote_range_instance(int tile_phi, int nk) {
+#define HT_VOTER_NK(S)                             \
+    switch (nk) {                                  \
+        case 64: return vote_range_fn<S, 64>();    \
+        case 128: return vote_range_fn<S, 128>();  \
+        case 256: return vote_range_fn<S, 256>();  \
+        case 512: return vote_range_fn<S, 512>();  \
+        default: return vote_range_fn<S, 0>();     \
+    }
+    switch (tile_phi) {
+        case 1: HT_VOTER_NK(1)
+        case 2: HT_VOTER_NK(2)
+        case 4: HT_VOTER_NK(4)
+        case 8: HT_VOTER_NK(8)
+    }
+#undef HT_VOTER_NK
+    return nullptr;
+}
+
 // kernel instance for (tile_phi, n_kappa): compile-time n_kappa for the common widths
 static void* vote_instance(int tile_phi, int nk) {
 #define HT_VOTE_NK(S)                         \
@@ -1118,8 +1504,13 @@ static void* vote_instance(int tile_phi, int nk) {
     return nullptr;
 }
 
-cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, bool band) {
-    void* f = band ? vote_band_instance(tile_phi, nk) : vote_instance(tile_phi, nk);
+static void* vote_variant(int tile_phi, int nk, int variant) {
+    return variant == 2 ? vote_range_instance(tile_phi, nk)
+                        : (variant == 1 ? vote_band_instance(tile_phi, nk) : vote_instance(tile_phi, nk));
+}
+
+cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant) {
+    void* f = vote_variant(tile_phi, nk, variant);
     if (!f) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
 }
@@ -1129,16 +1520,16 @@ cudaError_t launch_finalize(int64_t* scal, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t vote_prepare(int tile_phi, int nk, int smem, bool band) {
-    void* f = band ? vote_band_instance(tile_phi, nk) : vote_instance(tile_phi, nk);
+cudaError_t vote_prepare(int tile_phi, int nk, int smem, int variant) {
+    void* f = vote_variant(tile_phi, nk, variant);
     if (!f) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s,
-                        bool band) {
+                        int variant) {
     if (grid <= 0) return cudaSuccess;
-    void* f = band ? vote_band_instance(tile_phi, p.K.nk) : vote_instance(tile_phi, p.K.nk);
+    void* f = vote_variant(tile_phi, p.K.nk, variant);
     if (!f) return cudaErrorInvalidValue;
     void* args[] = {const_cast<VoteParams*>(&p)};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
@@ -1257,6 +1648,44 @@ cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int gr
     if ((int64_t)p.n_events * p.K.nphi == 0) return cudaSuccess;
     void* f = assoc_instance(tile_phi, p.K.nk, p.band != 0);
     if (!f) return cudaErrorInvalidValue;
+    const int smem = (int)(p.warp_bytes * (threads / 32));
+    void* args[] = {const_cast<AssocParams*>(&p)};
+    return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
+}
+
+template <int N, bool C>
+static void* assoc_range_fn() {
+    return reinterpret_cast<void*>(assoc_range_kernel<N, C>);
+}
+
+static void* assoc_range_instance(int nk, bool count) {
+    switch (nk) {
+        case 64: return count ? assoc_range_fn<64, true>() : assoc_range_fn<64, false>();
+        case 128: return count ? assoc_range_fn<128, true>() : assoc_range_fn<128, false>();
+        case 256: return count ? assoc_range_fn<256, true>() : assoc_range_fn<256, false>();
+        case 512: return count ? assoc_range_fn<512, true>() : assoc_range_fn<512, false>();
+        default: return count ? assoc_range_fn<0, true>() : assoc_range_fn<0, false>();
+    }
+}
+
+size_t assoc_range_warp_smem(int wd, int nk, int cap) { return assoc_range_warp_bytes(wd, nk, cap); }
+
+cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm) {
+    int b[2] = {0, 0};
+    for (int c = 0; c < 2; ++c) {
+        void* f = assoc_range_instance(nk, c != 0);
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[c], f, threads, smem);
+        if (e != cudaSuccess) return e;
+    }
+    *blocks_per_sm = std::min(b[0], b[1]);
+    return cudaSuccess;
+}
+
+cudaError_t launch_assoc_range(const AssocParams& p, bool count, int threads, int grid, cudaStream_t s) {
+    if ((int64_t)p.n_events * p.K.nphi == 0) return cudaSuccess;
+    void* f = assoc_range_instance(p.K.nk, count);
     const int smem = (int)(p.warp_bytes * (threads / 32));
     void* args[] = {const_cast<AssocParams*>(&p)};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);

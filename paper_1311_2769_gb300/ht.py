@@ -41,6 +41,10 @@ HT_OPT_LAUNCHES = 9
 HT_OPT_ATILE_PHI = 10
 HT_OPT_ATILE_D0 = 11
 HT_OPT_PRUNE = 12
+HT_OPT_VOTE_MODE = 13
+HT_OPT_ASSOC_CURSORS = 14
+HT_VOTE_POINT = 0
+HT_VOTE_RANGE = 1
 HT_MODE_BATCHED = 0
 HT_MODE_PLAIN = 1
 

@@ -458,6 +458,19 @@ def test_association_passes(ht, oracle_mod):
     _check_csr_rows(oracle_mod, g, b, pk, po, hi, 1, 1500)
 
 
+def test_association_cursor_passes_point(ht, oracle_mod):
+    """32 row cursors per warp against ~70 peaks per 32-column block: every
+    block is walked in passes, with the same CSR as with the default."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=3, first_event=60)
+    g = w.grid
+    full = _run(ht, g, b, w.threshold, 1)
+    small = _run(ht, g, b, w.threshold, 1, opts=((ht.HT_OPT_ASSOC_CURSORS, 32),))
+    for a, c in zip(full, small):
+        assert np.array_equal(a, c)
+    _check_csr_rows(oracle_mod, g, b, *small, 1, 400)
+
+
 def test_overflow_across_waves(ht):
     """Caps hit in the first wave: later waves lie wholly past the caps; the
     stored prefix and the true counts must match an unbounded run."""
