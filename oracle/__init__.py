@@ -70,6 +70,8 @@ def lib():
             "hto_range": (i32, [G, f, f, i32, i32, P, P]),
             "hto_vote_range": (None, [G, P, P, P, i32, P]),
             "hto_associate_range": (i64, [G, P, P, P, P, i64, i32, P, P, i64]),
+            "hto_fit": (None, [G, P, P, P, i64, P, P, P]),
+            "hto_fit_row": (None, [G, P, P, P, i64, i32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -272,3 +274,32 @@ def associate_range(g, x, y, event_offsets, pk, window):
         if n <= cap:
             return po, hi[:n].copy()
         cap = n
+
+
+# ---- circle fit ------------------------------------------------------------
+
+TRACK_DTYPE = np.dtype([("status", np.int32), ("n_hits", np.int32), ("cos_phi0", np.float64),
+                        ("sin_phi0", np.float64), ("d0", np.float64), ("kappa", np.float64),
+                        ("chi2", np.float64)])
+
+
+def fit(g, x, y, pk, peak_offsets, hit_idx) -> np.ndarray:
+    """Circle fit of every candidate's CSR row: structured array TRACK_DTYPE."""
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    pk = np.ascontiguousarray(pk, dtype=PEAK_DTYPE)
+    po = np.ascontiguousarray(peak_offsets, dtype=np.int64)
+    hi = np.ascontiguousarray(hit_idx, dtype=np.int32)
+    out = np.zeros(pk.shape[0], TRACK_DTYPE)
+    lib().hto_fit(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(pk), pk.shape[0], _ptr(po), _ptr(hi), _ptr(out))
+    return out
+
+
+def fit_hits(g, x, y, i_kappa) -> np.void:
+    """Circle fit of the given hits (all of them, in order) for a peak in kappa bin i_kappa."""
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    idx = np.arange(x.shape[0], dtype=np.int32)
+    out = np.zeros(1, TRACK_DTYPE)
+    lib().hto_fit_row(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(idx), x.shape[0], int(i_kappa), _ptr(out))
+    return out[0]

@@ -463,3 +463,83 @@ int64_t hto_associate_range(const hto_grid *g, const float *x, const float *y,
     free(ce); free(se); free(de);
     return n;
 }
+
+/* ---- circle fit of a candidate's hits (the second extension) -------------
+ *
+ * Section 3: the HT candidates seed a confirmation fit.  Reading used here:
+ * the algebraic (Kasa) least-squares circle through the candidate's
+ * associated hits, x^2 + y^2 + D x + E y + F = 0 minimising the sum of the
+ * squared left-hand sides, solved from its 3 x 3 normal equations by
+ * Cramer's rule; sums run over the row's hits in ascending order, every
+ * operation one binary64 IEEE operation in the order written.  The circle
+ * becomes perigee parameters with the turning sign s of the peak's kappa bin
+ * centre (s = +1 when that centre is >= 0): kappa = s / R, unit normal
+ * n = s C / |C|, d0 = s (|C| - R), phi0 from n = (-sin phi0, cos phi0); the
+ * outputs are cos phi0, sin phi0, d0, kappa and the geometric chi^2 =
+ * sum (|h - C| - R)^2.  status: 1 fitted, 0 fewer than three hits or a
+ * singular system or R^2 <= 0 or C = 0.
+ */
+void hto_fit_row(const hto_grid *g, const float *x, const float *y, const int32_t *idx, int64_t n,
+                 int32_t i_kappa, hto_track *out)
+{
+    memset(out, 0, sizeof(*out));
+    out->n_hits = (int32_t)n;
+    if (n < 3)
+        return;
+    double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0, syy = 0.0, sz = 0.0, sxz = 0.0, syz = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        double a = x[idx[t]], b = y[idx[t]];
+        double z = (a * a) + (b * b);
+        sx = sx + a;
+        sy = sy + b;
+        sxx = sxx + (a * a);
+        sxy = sxy + (a * b);
+        syy = syy + (b * b);
+        sz = sz + z;
+        sxz = sxz + (a * z);
+        syz = syz + (b * z);
+    }
+    double nn = (double)n;
+    /* M (D E F)^T = -(sxz, syz, sz)^T, M = [[sxx sxy sx] [sxy syy sy] [sx sy n]] */
+    double c00 = (syy * nn) - (sy * sy);
+    double c01 = (sxy * nn) - (sy * sx);
+    double c02 = (sxy * sy) - (syy * sx);
+    double det = ((sxx * c00) - (sxy * c01)) + (sx * c02);
+    if (!(det != 0.0))
+        return;
+    double r0 = -sxz, r1 = -syz, r2 = -sz;
+    /* Cramer: replace one column by r */
+    double dD = ((r0 * c00) - (sxy * ((r1 * nn) - (sy * r2)))) + (sx * ((r1 * sy) - (syy * r2)));
+    double dE = ((sxx * ((r1 * nn) - (sy * r2))) - (r0 * c01)) + (sx * ((sxy * r2) - (r1 * sx)));
+    double dF = ((sxx * ((syy * r2) - (r1 * sy))) - (sxy * ((sxy * r2) - (r1 * sx)))) + (r0 * c02);
+    double D = dD / det, E = dE / det, F = dF / det;
+    double cx = -0.5 * D, cy = -0.5 * E;
+    double R2 = ((cx * cx) + (cy * cy)) - F;
+    double rho = sqrt((cx * cx) + (cy * cy));
+    if (!(R2 > 0.0) || !(rho > 0.0))
+        return;
+    double R = sqrt(R2);
+    double kc = (double)g->kappa_min + (((double)i_kappa + 0.5) * (((double)g->kappa_max - (double)g->kappa_min) / (double)g->n_kappa));
+    double s = kc >= 0.0 ? 1.0 : -1.0;
+    double nx = (s * cx) / rho, ny = (s * cy) / rho;
+    double chi2 = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        double a = (double)x[idx[t]] - cx, b = (double)y[idx[t]] - cy;
+        double r = sqrt((a * a) + (b * b)) - R;
+        chi2 = chi2 + (r * r);
+    }
+    out->status = 1;
+    out->cos_phi0 = ny;
+    out->sin_phi0 = -nx;
+    out->d0 = s * (rho - R);
+    out->kappa = s / R;
+    out->chi2 = chi2;
+}
+
+void hto_fit(const hto_grid *g, const float *x, const float *y, const hto_peak *peaks, int64_t n_peaks,
+             const int64_t *peak_offsets, const int32_t *hit_idx, hto_track *out)
+{
+    for (int64_t p = 0; p < n_peaks; ++p)
+        hto_fit_row(g, x, y, hit_idx + peak_offsets[p], peak_offsets[p + 1] - peak_offsets[p],
+                    peaks[p].i_kappa, &out[p]);
+}

@@ -129,6 +129,21 @@ int64_t hto_associate_range(const hto_grid *g, const float *x, const float *y,
                             const int32_t *event_offsets, const hto_peak *peaks, int64_t n_peaks,
                             int32_t window, int64_t *peak_offsets, int32_t *hit_idx, int64_t cap);
 
+/* ---- circle fit ----------------------------------------------------------
+ * Algebraic least-squares circle through a candidate's hits (binary64, sums
+ * in row order, Cramer's rule), as perigee parameters with the turning sign
+ * of the peak's kappa bin centre.  status 1 fitted, 0 not (< 3 hits, singular
+ * system, R^2 <= 0, centre at the origin). */
+typedef struct {
+    int32_t status, n_hits;
+    double cos_phi0, sin_phi0, d0, kappa, chi2;
+} hto_track;
+
+void hto_fit_row(const hto_grid *g, const float *x, const float *y, const int32_t *idx, int64_t n,
+                 int32_t i_kappa, hto_track *out);
+void hto_fit(const hto_grid *g, const float *x, const float *y, const hto_peak *peaks, int64_t n_peaks,
+             const int64_t *peak_offsets, const int32_t *hit_idx, hto_track *out);
+
 #ifdef __cplusplus
 }
 #endif
