@@ -331,6 +331,21 @@ def run_gpu(args):
         ms = float(t.item())
     launches = ctx.get_option(ht.HT_OPT_LAUNCHES)
     counts = res.counts.cpu().numpy()
+    # circle fit of the stored candidates of the last step (not in the step)
+    fit_ms = []
+    for _ in range(3):
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        fits = ctx.fit(res, stream=stream)
+        f1.record(stream)
+        f1.synchronize()
+        fit_ms.append(f0.elapsed_time(f1))
+    n_fit = int(min(counts[0], res.peak_cap))
+    fitted = int((fits.view(torch.int32)[0::12][:n_fit] == 1).sum().item())  # status, every 48 bytes
+    fit_info = {"ms": float(np.median(fit_ms)), "candidates": n_fit, "fitted": fitted,
+                "candidates_per_s": n_fit / (float(np.median(fit_ms)) / 1e3)}
+    del fits
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_events / (ms / 1e3), "ms_per_step": ms,
@@ -464,6 +479,7 @@ def run_gpu(args):
         "e2e": e2e,
         "serving": serving,
         "range_vote": range_vote,
+        "fit": fit_info,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, batch)

@@ -222,6 +222,26 @@ int ht_sync(ht_ctx *ctx);
  * the sample must fit the accumulator budget. */
 int ht_autotune(ht_ctx *ctx, const ht_hits *hits, void *stream);
 
+/* Circle fit of the candidates of the last ht_process, whose outputs are
+ * `res` (the confirmation fit Section 3 hands the candidates to; this
+ * library's reading, not a formula of the paper): for each stored candidate
+ * c < min(n_peaks, peak_cap, cap), the algebraic least-squares circle
+ * x^2 + y^2 + D x + E y + F = 0 through the hits of its CSR row (sums over
+ * the row in order, Cramer's rule, every step one binary64 IEEE operation),
+ * as perigee parameters with the turning sign s of the peak's kappa bin
+ * centre: kappa = s / R, unit normal n = s C / |C| = (-sin phi0, cos phi0),
+ * d0 = s (|C| - R), chi2 = sum (|h - C| - R)^2.  status 1 fitted; 0 fewer
+ * than 3 hits, a singular system, R^2 <= 0 or a centre at the origin; -1 the
+ * row lost hits to pair_cap.  The hits are those of that ht_process (device
+ * hits must still be valid).  out[cap] lives in res->mem: with device
+ * results the call is asynchronous on `stream`, with host results it
+ * synchronises. */
+typedef struct {
+    int32_t status, n_hits;
+    double cos_phi0, sin_phi0, d0, kappa, chi2;
+} ht_track;
+int ht_fit(ht_ctx *ctx, const ht_results *res, ht_track *out, int64_t cap, void *stream);
+
 /* Device time of the last single-wave ht_process (needs HT_OPT_PHASE_TIMING=1,
  * read after ht_sync), into ms[4]: ms[0] vote kernel, ms[1] peaks +
  * association, ms[2] whole device step, ms[3] association kernel (with its

@@ -123,7 +123,8 @@ struct ht_ctx {
     int32_t c_events = 0;
     int32_t c_event0 = 0;  // first event of the accumulators held (ht_vote: 0)
     int32_t c_wave_events = 0;
-    bool have_votes = false, have_peaks = false;
+    bool have_votes = false, have_peaks = false, have_results = false;
+    DBuf<ht_track> fits;  // device staging of fits for host results
     int64_t n_peaks_held = 0;
     uint32_t last_threshold = 0;
 
@@ -818,6 +819,7 @@ int ht_destroy(ht_ctx* ctx) {
     ctx->peaks.release();
     ctx->peakoff.release();
     ctx->hitidx.release();
+    ctx->fits.release();
     ctx->scratch.release();
     delete ctx;
     return HT_OK;
@@ -922,7 +924,7 @@ int ht_vote(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     int st = stage_hits(ctx, hits, s);
     if (st) return st;
     ctx->stream = s;
-    ctx->have_votes = ctx->have_peaks = false;
+    ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
     st = ensure_wave_buffers(ctx, ctx->c_events);
     if (st) return st;
     const bool plain = ctx->mode == HT_MODE_PLAIN;
@@ -1039,7 +1041,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
     int st = stage_hits(ctx, hits, s);
     if (st) return st;
     ctx->stream = s;
-    ctx->have_votes = ctx->have_peaks = false;
+    ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
     const int32_t epw = events_per_wave(ctx, ctx->c_events);
     if (epw < 1)
         return fail(ctx, HT_ERR_BUDGET, "one accumulator (%lld B) exceeds the budget", (long long)(ctx->cells * 4));
@@ -1107,6 +1109,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, epw, s);
         if (st) return st;
     }
+    ctx->have_results = true;
     // counts = {peak total, pair total + pairs of peaks beyond the cap}
     if (res->mem == HT_DEVICE) {
         CU(cudaMemcpyAsync(res->counts, ctx->d_scal + 6, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
@@ -1170,6 +1173,46 @@ int ht_get_tables(ht_ctx* ctx, float* cos_phi, float* sin_phi, float* d0) {
     if (cos_phi) std::memcpy(cos_phi, ctx->h_cphi.data(), ctx->h_cphi.size() * sizeof(float));
     if (sin_phi) std::memcpy(sin_phi, ctx->h_sphi.data(), ctx->h_sphi.size() * sizeof(float));
     if (d0) std::memcpy(d0, ctx->h_d0.data(), ctx->h_d0.size() * sizeof(float));
+    return HT_OK;
+}
+
+int ht_fit(ht_ctx* ctx, const ht_results* res, ht_track* out, int64_t cap, void* stream) {
+    if (!ctx || !res || cap < 0 || (cap > 0 && !out)) return HT_ERR_INVALID_ARG;
+    if (res->mem != HT_HOST && res->mem != HT_DEVICE) return fail(ctx, HT_ERR_INVALID_ARG, "res.mem must be HT_HOST or HT_DEVICE");
+    if (!ctx->have_results) return fail(ctx, HT_ERR_STATE, "ht_fit needs a preceding ht_process");
+    cudaStream_t s = nullptr;
+    if (int st0 = resolve_stream(ctx, stream, &s)) return st0;
+    FitParams p{};
+    p.x = ctx->cx;
+    p.y = ctx->cy;
+    p.peak_cap = res->peak_cap;
+    p.pair_cap = res->pair_cap;
+    p.cap = cap;
+    p.kmin = (double)ctx->grid.kappa_min;
+    p.kmax = (double)ctx->grid.kappa_max;
+    p.nk = ctx->grid.n_kappa;
+    if (res->mem == HT_DEVICE) {
+        p.peaks = res->peaks;
+        p.po = res->peak_offsets;
+        p.hidx = res->hit_idx;
+        p.n_peaks = res->counts;
+        p.out = out;
+        CU(launch_fit(p, s));
+        return HT_OK;
+    }
+    // host results: the context still holds them on the device
+    const int64_t n = std::min(std::min(res->counts[0], res->peak_cap), cap);
+    if (n <= 0) return HT_OK;
+    CU(ctx->fits.ensure(n, &ctx->gen));
+    p.peaks = ctx->peaks.p;
+    p.po = ctx->peakoff.p;
+    p.hidx = ctx->hitidx.p;
+    p.n_peaks = ctx->d_scal + 6;
+    p.cap = n;
+    p.out = ctx->fits.p;
+    CU(launch_fit(p, s));
+    CU(cudaMemcpyAsync(out, ctx->fits.p, n * sizeof(ht_track), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
     return HT_OK;
 }
 
@@ -1306,7 +1349,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->gvalid = false;
-    ctx->have_votes = ctx->have_peaks = false;
+    ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
     return resolve_tiles(ctx);
 }
 

@@ -125,6 +125,20 @@ cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int gr
 size_t assoc_range_warp_smem(int wd, int nk, int cap);
 cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm);
 cudaError_t launch_assoc_range(const AssocParams& p, bool count, int threads, int grid, cudaStream_t s);
+// circle fit of the stored candidates' rows (ht_fit.cu)
+struct FitParams {
+    const float* x;
+    const float* y;
+    const ht_peak* peaks;
+    const int64_t* po;       // CSR offsets [peak_cap + 1]
+    const int32_t* hidx;
+    const int64_t* n_peaks;  // device scalar: the true peak count
+    int64_t peak_cap, pair_cap, cap;
+    ht_track* out;
+    double kmin, kmax;
+    int32_t nk;
+};
+cudaError_t launch_fit(const FitParams& p, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
 
 }  // namespace ht

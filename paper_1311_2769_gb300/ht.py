@@ -50,10 +50,14 @@ HT_MODE_PLAIN = 1
 
 EXPORTS = ("ht_create", "ht_destroy", "ht_set_option", "ht_get_option", "ht_vote", "ht_peaks",
            "ht_associate", "ht_process", "ht_get_accumulator", "ht_get_tables", "ht_sync",
-           "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_peaks_noalloc", "ht_check_rcp", "ht_strerror", "ht_last_error")
+           "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_peaks_noalloc", "ht_check_rcp", "ht_strerror", "ht_last_error",
+           "ht_fit")
 
 PEAK_DTYPE = np.dtype([("event", np.int32), ("i_phi", np.int32), ("i_d0", np.int32),
                        ("i_kappa", np.int32), ("votes", np.uint32)])
+TRACK_DTYPE = np.dtype([("status", np.int32), ("n_hits", np.int32), ("cos_phi0", np.float64),
+                        ("sin_phi0", np.float64), ("d0", np.float64), ("kappa", np.float64),
+                        ("chi2", np.float64)])
 
 
 class HtGeometry(ctypes.Structure):
@@ -113,6 +117,7 @@ def load() -> ctypes.CDLL:
         "ht_phase_times": [P, P],
         "ht_check_rcp": [u32, u32, P],
         "ht_peaks_noalloc": [P, P, i32, u32, P, i64, P, P],
+        "ht_fit": [P, P, P, i64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -353,6 +358,27 @@ def ht_peaks_noalloc(grid, acc, n_events, threshold, peaks, cap, count, stream=N
                                           int(cap), _ptr(count), _stream_ptr(stream)))
 
 
+def ht_fit(ctx, results, cap=None, stream=None):
+    """Circle fits of the candidates in `results` (see ht.h): a TRACK_DTYPE
+    array for host results, else a CUDA uint8 tensor of cap * 48 bytes
+    (tracks_host() reads it back)."""
+    cap = results.peak_cap if cap is None else int(cap)
+    if isinstance(results.counts, np.ndarray):
+        n = int(min(results.counts[0], results.peak_cap, cap))
+        out = np.zeros(max(n, 1), TRACK_DTYPE)
+        _check(load().ht_fit(ctx, ctypes.byref(results.struct), out.ctypes.data, n, _stream_ptr(stream)), ctx)
+        return out[:n]
+    import torch
+    out = torch.zeros(max(cap, 1) * TRACK_DTYPE.itemsize, dtype=torch.uint8, device=results.counts.device)
+    _check(load().ht_fit(ctx, ctypes.byref(results.struct), _ptr(out), cap, _stream_ptr(stream)), ctx)
+    return out
+
+
+def tracks_host(t, n):
+    """The first n fits of a device fit buffer as a TRACK_DTYPE array."""
+    return np.frombuffer(t.cpu().numpy().tobytes(), TRACK_DTYPE)[: int(n)].copy()
+
+
 def ht_check_rcp(first_bits, count):
     out = np.zeros(2, np.uint64)
     _check(load().ht_check_rcp(int(first_bits), int(count), out.ctypes.data))
@@ -413,3 +439,6 @@ class Context:
 
     def phase_times(self):
         return ht_phase_times(self.handle)
+
+    def fit(self, results, cap=None, stream=None):
+        return ht_fit(self.handle, results, cap, stream)
