@@ -37,6 +37,11 @@ class Grid(ctypes.Structure):
                 ("kappa_min", ctypes.c_float), ("kappa_max", ctypes.c_float)]
 
 
+class VGrid(ctypes.Structure):
+    _fields_ = [("n_x", ctypes.c_int32), ("n_y", ctypes.c_int32), ("x_min", ctypes.c_float),
+                ("x_max", ctypes.c_float), ("y_min", ctypes.c_float), ("y_max", ctypes.c_float)]
+
+
 PEAK_DTYPE = np.dtype([("event", np.int32), ("i_phi", np.int32), ("i_d0", np.int32),
                        ("i_kappa", np.int32), ("votes", np.uint32)])
 
@@ -72,6 +77,8 @@ def lib():
             "hto_associate_range": (i64, [G, P, P, P, P, i64, i32, P, P, i64]),
             "hto_fit": (None, [G, P, P, P, i64, P, P, P]),
             "hto_fit_row": (None, [G, P, P, P, i64, i32, P]),
+            "hto_vertex_vote": (None, [G, ctypes.POINTER(VGrid), P, i64, i32, P]),
+            "hto_vertex_peaks": (i64, [ctypes.POINTER(VGrid), P, i32, u32, P, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -303,3 +310,34 @@ def fit_hits(g, x, y, i_kappa) -> np.void:
     out = np.zeros(1, TRACK_DTYPE)
     lib().hto_fit_row(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(idx), x.shape[0], int(i_kappa), _ptr(out))
     return out[0]
+
+
+# ---- second Hough transform: displaced vertices ------------------------------
+
+VERTEX_DTYPE = np.dtype([("event", np.int32), ("i_x", np.int32), ("i_y", np.int32), ("votes", np.uint32)])
+
+
+def vgrid_struct(v) -> VGrid:
+    """Any object with n_x, n_y, x_min, x_max, y_min, y_max."""
+    return VGrid(int(v.n_x), int(v.n_y), float(v.x_min), float(v.x_max), float(v.y_min), float(v.y_max))
+
+
+def vertex_vote(g, v, pk, n_events) -> np.ndarray:
+    """Vertex accumulators [n_events, n_x, n_y] uint32 from the candidates pk."""
+    gs, vs = grid_struct(g), vgrid_struct(v)
+    pk = np.ascontiguousarray(pk, dtype=PEAK_DTYPE)
+    acc = np.empty((int(n_events), vs.n_x, vs.n_y), np.uint32)
+    lib().hto_vertex_vote(ctypes.byref(gs), ctypes.byref(vs), _ptr(pk), pk.shape[0], int(n_events), _ptr(acc))
+    return acc
+
+
+def vertex_peaks(v, acc, threshold) -> np.ndarray:
+    vs = vgrid_struct(v)
+    acc = np.ascontiguousarray(acc, dtype=np.uint32)
+    cap = 1024
+    while True:
+        out = np.empty(cap, VERTEX_DTYPE)
+        n = lib().hto_vertex_peaks(ctypes.byref(vs), _ptr(acc), acc.shape[0], int(threshold), _ptr(out), cap)
+        if n <= cap:
+            return out[:n].copy()
+        cap = n

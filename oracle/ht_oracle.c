@@ -543,3 +543,109 @@ void hto_fit(const hto_grid *g, const float *x, const float *y, const hto_peak *
         hto_fit_row(g, x, y, hit_idx + peak_offsets[p], peak_offsets[p + 1] - peak_offsets[p],
                     peaks[p].i_kappa, &out[p]);
 }
+
+/* ---- second Hough transform: displaced vertices (the third extension) -----
+ *
+ * Section "Displaced vertex identification": tracks from a common vertex
+ * (xv, yv) satisfy d0 = yv cos phi0 - xv sin phi0, a sinusoid in the first
+ * transform's (phi0, d0) space, and a second Hough transform of the first
+ * one's maxima finds them.  Reading used here: every candidate (peak) votes,
+ * with its cell's centre tables (cos phi_i, sin phi_i, d0_j as floats), for
+ * the cells of an (x, y) vertex grid that its line y c - x s = d crosses,
+ * walking the axis along which the line is less steep: when |c| >= |s|, for
+ * each x bin centre X the y of the line (d + X s) / c, else for each y bin
+ * centre Y the x of the line (Y c - d) / s; one vote per bin of the walked
+ * axis whose other coordinate falls inside the grid.  Every operation is one
+ * binary64 IEEE operation in the order written.  Vertices are the local
+ * maxima of each event's (x, y) accumulator at or above a threshold, by the
+ * first transform's rule: strictly above the neighbours preceding in linear
+ * (x, y) order, at least the ones following, 8-neighbourhood, no wrap.
+ */
+static void vgrid_centres(const hto_vgrid *v, double *xc, double *yc)
+{
+    double wx = ((double)v->x_max - (double)v->x_min) / (double)v->n_x;
+    double wy = ((double)v->y_max - (double)v->y_min) / (double)v->n_y;
+    for (int32_t a = 0; a < v->n_x; ++a)
+        xc[a] = (double)v->x_min + (((double)a + 0.5) * wx);
+    for (int32_t b = 0; b < v->n_y; ++b)
+        yc[b] = (double)v->y_min + (((double)b + 0.5) * wy);
+}
+
+static int32_t vbin(double u, float lo, float hi, int32_t n)
+{
+    double t = (u - (double)lo) * ((double)n / ((double)hi - (double)lo));
+    if (!(t >= 0.0 && t < (double)n))
+        return -1;
+    return (int32_t)t;
+}
+
+void hto_vertex_vote(const hto_grid *g, const hto_vgrid *v, const hto_peak *peaks, int64_t n_peaks,
+                     int32_t n_events, uint32_t *acc)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    double *xc = (double *)malloc(sizeof(double) * (size_t)v->n_x);
+    double *yc = (double *)malloc(sizeof(double) * (size_t)v->n_y);
+    vgrid_centres(v, xc, yc);
+    const int64_t cells = (int64_t)v->n_x * v->n_y;
+    memset(acc, 0, sizeof(uint32_t) * (size_t)(cells * n_events));
+    for (int64_t p = 0; p < n_peaks; ++p) {
+        const hto_peak *pk = &peaks[p];
+        if (pk->event < 0 || pk->event >= n_events)
+            continue;
+        uint32_t *a1 = acc + (int64_t)pk->event * cells;
+        double cc = c[pk->i_phi], ss = s[pk->i_phi], dd = d[pk->i_d0];
+        if (fabs(cc) >= fabs(ss)) {
+            for (int32_t a = 0; a < v->n_x; ++a) {
+                int32_t b = vbin((dd + (xc[a] * ss)) / cc, v->y_min, v->y_max, v->n_y);
+                if (b >= 0)
+                    a1[(int64_t)a * v->n_y + b] += 1u;
+            }
+        } else {
+            for (int32_t b = 0; b < v->n_y; ++b) {
+                int32_t a = vbin(((yc[b] * cc) - dd) / ss, v->x_min, v->x_max, v->n_x);
+                if (a >= 0)
+                    a1[(int64_t)a * v->n_y + b] += 1u;
+            }
+        }
+    }
+    free(xc); free(yc); free(c); free(s); free(d);
+}
+
+int64_t hto_vertex_peaks(const hto_vgrid *v, const uint32_t *acc, int32_t n_events, uint32_t threshold,
+                         hto_vertex *out, int64_t cap)
+{
+    const int64_t cells = (int64_t)v->n_x * v->n_y;
+    int64_t n = 0;
+    for (int32_t e = 0; e < n_events; ++e) {
+        const uint32_t *a1 = acc + (int64_t)e * cells;
+        for (int32_t a = 0; a < v->n_x; ++a)
+            for (int32_t b = 0; b < v->n_y; ++b) {
+                const int64_t self = (int64_t)a * v->n_y + b;
+                const uint32_t val = a1[self];
+                if (val < threshold)
+                    continue;
+                int ok = 1;
+                for (int da = -1; da <= 1 && ok; ++da)
+                    for (int db = -1; db <= 1; ++db) {
+                        int32_t aa = a + da, bb = b + db;
+                        if ((da == 0 && db == 0) || aa < 0 || aa >= v->n_x || bb < 0 || bb >= v->n_y)
+                            continue;
+                        const int64_t other = (int64_t)aa * v->n_y + bb;
+                        const uint32_t u = a1[other];
+                        if (other < self ? !(val > u) : !(val >= u)) {
+                            ok = 0;
+                            break;
+                        }
+                    }
+                if (ok) {
+                    if (n < cap) {
+                        hto_vertex t = {e, a, b, val};
+                        out[n] = t;
+                    }
+                    ++n;
+                }
+            }
+    }
+    return n;
+}

@@ -144,6 +144,28 @@ void hto_fit_row(const hto_grid *g, const float *x, const float *y, const int32_
 void hto_fit(const hto_grid *g, const float *x, const float *y, const hto_peak *peaks, int64_t n_peaks,
              const int64_t *peak_offsets, const int32_t *hit_idx, hto_track *out);
 
+/* ---- second Hough transform: displaced vertices --------------------------
+ * Every candidate votes along its line y cos(phi_i) - x sin(phi_i) = d0_j in
+ * an (x, y) grid, walking the less steep axis (binary64); vertices are the
+ * 2-D local maxima at or above a threshold (linear-order tie rule,
+ * 8-neighbourhood, no wrap). */
+typedef struct {
+    int32_t n_x, n_y;
+    float x_min, x_max, y_min, y_max;
+} hto_vgrid;
+
+typedef struct {
+    int32_t event, i_x, i_y;
+    uint32_t votes;
+} hto_vertex;
+
+/* acc is [n_events][n_x][n_y] uint32, zeroed here; peaks of events outside
+ * [0, n_events) are ignored. */
+void hto_vertex_vote(const hto_grid *g, const hto_vgrid *v, const hto_peak *peaks, int64_t n_peaks,
+                     int32_t n_events, uint32_t *acc);
+int64_t hto_vertex_peaks(const hto_vgrid *v, const uint32_t *acc, int32_t n_events, uint32_t threshold,
+                         hto_vertex *out, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif
