@@ -209,6 +209,71 @@ def range_vote_report(dev, n_batch=256, n_single=64):
     return out
 
 
+def vertex_report(dev, n_jets=64, n_batch=512):
+    """Second Hough transform: device time and vertex finding on events of
+    four displaced jets of straight tracks (the paper's picture; a true
+    vertex counts as found when a vertex lies within two cells), and device
+    time on a sample of the batch workload's candidates."""
+    import collections
+    import torch
+    from paper_1311_2769_gb300 import ht, synth
+    VG = collections.namedtuple("VG", "n_x n_y x_min x_max y_min y_max")
+    vg = VG(64, 64, -32.0, 32.0, -32.0, 32.0)
+    rng = np.random.default_rng(2024)
+    xs, ys, offs, verts = [], [], [0], []
+    for _ in range(n_jets):
+        vs = rng.uniform(-20, 20, (4, 2))
+        phi0, d0, kap = [], [], []
+        for xv, yv in vs:
+            axis = math.atan2(yv, xv)
+            for _ in range(8):
+                psi = axis + rng.uniform(-0.6, 0.6)
+                phi0.append(psi % (2 * math.pi))
+                d0.append(yv * math.cos(psi) - xv * math.sin(psi))
+                kap.append(rng.uniform(-1e-5, 1e-5))
+        x, y, _, ok = synth.helix_hits(phi0, d0, kap, synth.LAYERS_13)
+        xs.append(x[ok].astype(np.float32))
+        ys.append(y[ok].astype(np.float32))
+        offs.append(offs[-1] + xs[-1].shape[0])
+        verts.append(vs)
+    jets = synth.from_arrays(np.concatenate(xs), np.concatenate(ys), event_offsets=np.array(offs, np.int32))
+    out = {}
+    for name, b, g, thr, vthr in (
+            ("displaced_jets", jets, synth.Grid(256, 64, 1, -40.0, 40.0, -0.0005, 0.0005), 9, 6),
+            ("batch_4096_lognormal", synth.generate(synth.WORKLOADS[WORKLOAD], n_events=n_batch),
+             synth.WORKLOADS[WORKLOAD].grid, synth.WORKLOADS[WORKLOAD].threshold, 40)):
+        ctx = ht.Context(g, synth.LAYERS_13)
+        res = ht.Results(b.n_events * 20000 + 4096, b.n_events * 800000 + 65536, device=dev)
+        ctx.process(ht.Hits.from_batch(b, device=dev), thr, 1, res)
+        ctx.sync()
+        ms = []
+        s = torch.cuda.current_stream()
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            vo, cnt = ctx.vertices(vg, res, vthr, cap=1 << 20, stream=s)
+            e1.record(s)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        n = int(cnt.item())
+        row = {"events": b.n_events, "candidates": int(res.counts[0].item()), "vertex_threshold": vthr,
+               "ms": float(np.median(ms)), "vertices": n}
+        if name == "displaced_jets":
+            got = ht.vertices_host(vo, min(n, 1 << 20))
+            found = 0
+            for e, vs in enumerate(verts):
+                ev = got[got["event"] == e]
+                for xv, yv in vs:
+                    a, c = int((xv + 32.0) // 1.0), int((yv + 32.0) // 1.0)
+                    found += int(np.any((np.abs(ev["i_x"] - a) <= 2) & (np.abs(ev["i_y"] - c) <= 2)))
+            row["true_vertices"] = 4 * len(verts)
+            row["found"] = found
+        out[name] = row
+        ctx.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
     rank, world, _ = _dist()
@@ -430,6 +495,14 @@ def run_gpu(args):
         except Exception as e:  # report, do not hide, a failing measurement
             range_vote = {"error": f"{type(e).__name__}: {e}"}
 
+    # ---- second Hough transform (rank 0, N=1)
+    vertex = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        try:
+            vertex = vertex_report(dev)
+        except Exception as e:
+            vertex = {"error": f"{type(e).__name__}: {e}"}
+
     # ---- roofline of the dominant kernel (association) and of the vote:
     # issue-bound ALU work, 6 ops per (hit, phi0, d0) cell of the method
     peaks, peak_src = _peaks()
@@ -480,6 +553,7 @@ def run_gpu(args):
         "serving": serving,
         "range_vote": range_vote,
         "fit": fit_info,
+        "vertex": vertex,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, batch)

@@ -242,6 +242,33 @@ typedef struct {
 } ht_track;
 int ht_fit(ht_ctx *ctx, const ht_results *res, ht_track *out, int64_t cap, void *stream);
 
+/* Second Hough transform for displaced vertices (Section "Displaced vertex
+ * identification": tracks from a common vertex (xv, yv) satisfy
+ * d0 = yv cos phi0 - xv sin phi0, and a second transform of the first one's
+ * maxima finds it).  The stored candidates of the last ht_process, whose
+ * outputs are `res`, vote with their cells' centre tables for the cells of
+ * the (x, y) grid `vg` that their line y cos phi_i - x sin phi_i = d0_j
+ * crosses, walking the axis along which the line is less steep (one vote per
+ * bin of that axis whose other coordinate lies inside the grid; binary64).
+ * Vertices are the local maxima of each event's [n_x][n_y] accumulator at or
+ * above `threshold`: strictly above the neighbours preceding in linear
+ * (x, y) order, at least the ones following, 8-neighbourhood, no wrap;
+ * written to out[cap] in ascending (event, linear index) order, the true
+ * number to *count.  out and count live in res->mem (device: asynchronous on
+ * `stream`; host: synchronous).  The accumulators stay in the context. */
+typedef struct {
+    int32_t n_x, n_y;
+    float x_min, x_max, y_min, y_max;
+} ht_vgrid;
+
+typedef struct {
+    int32_t event, i_x, i_y;
+    uint32_t votes;
+} ht_vertex;
+
+int ht_vertices(ht_ctx *ctx, const ht_vgrid *vg, const ht_results *res, uint32_t threshold, ht_vertex *out,
+                int64_t cap, int64_t *count, void *stream);
+
 /* Device time of the last single-wave ht_process (needs HT_OPT_PHASE_TIMING=1,
  * read after ht_sync), into ms[4]: ms[0] vote kernel, ms[1] peaks +
  * association, ms[2] whole device step, ms[3] association kernel (with its

@@ -125,6 +125,12 @@ struct ht_ctx {
     int32_t c_wave_events = 0;
     bool have_votes = false, have_peaks = false, have_results = false;
     DBuf<ht_track> fits;  // device staging of fits for host results
+    // second Hough transform: accumulators, per-row counts and bases, scalars, staging
+    DBuf<uint32_t> vacc;
+    DBuf<int32_t> vrow;
+    DBuf<int64_t> vbase;
+    DBuf<int64_t> vscal;
+    DBuf<ht_vertex> vout;
     int64_t n_peaks_held = 0;
     uint32_t last_threshold = 0;
 
@@ -820,6 +826,11 @@ int ht_destroy(ht_ctx* ctx) {
     ctx->peakoff.release();
     ctx->hitidx.release();
     ctx->fits.release();
+    ctx->vacc.release();
+    ctx->vrow.release();
+    ctx->vbase.release();
+    ctx->vscal.release();
+    ctx->vout.release();
     ctx->scratch.release();
     delete ctx;
     return HT_OK;
@@ -1213,6 +1224,81 @@ int ht_fit(ht_ctx* ctx, const ht_results* res, ht_track* out, int64_t cap, void*
     CU(launch_fit(p, s));
     CU(cudaMemcpyAsync(out, ctx->fits.p, n * sizeof(ht_track), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    return HT_OK;
+}
+
+int ht_vertices(ht_ctx* ctx, const ht_vgrid* vg, const ht_results* res, uint32_t threshold, ht_vertex* out,
+                int64_t cap, int64_t* count, void* stream) {
+    if (!ctx || !vg || !res || !count || cap < 0 || (cap > 0 && !out)) return HT_ERR_INVALID_ARG;
+    if (vg->n_x < 1 || vg->n_y < 1 || vg->n_x > 65535 || vg->n_y > 65535 || !std::isfinite(vg->x_min) ||
+        !std::isfinite(vg->x_max) || !std::isfinite(vg->y_min) || !std::isfinite(vg->y_max) ||
+        !(vg->x_max > vg->x_min) || !(vg->y_max > vg->y_min))
+        return fail(ctx, HT_ERR_INVALID_ARG, "bad vertex grid");
+    if (res->mem != HT_HOST && res->mem != HT_DEVICE) return fail(ctx, HT_ERR_INVALID_ARG, "res.mem must be HT_HOST or HT_DEVICE");
+    if (!ctx->have_results) return fail(ctx, HT_ERR_STATE, "ht_vertices needs a preceding ht_process");
+    cudaStream_t s = nullptr;
+    if (int st0 = resolve_stream(ctx, stream, &s)) return st0;
+    const int64_t ne = ctx->c_events;
+    const int64_t cells = ne * vg->n_x * vg->n_y, rows = ne * vg->n_x;
+    CU(ctx->vacc.ensure(std::max<int64_t>(cells, 1), nullptr));
+    CU(ctx->vrow.ensure(std::max<int64_t>(rows, 1), nullptr));
+    CU(ctx->vbase.ensure(rows + 1, nullptr));
+    CU(ctx->vscal.ensure(2, nullptr));
+    CU(cudaMemsetAsync(ctx->vacc.p, 0, std::max<int64_t>(cells, 1) * sizeof(uint32_t), s));
+    CU(cudaMemsetAsync(ctx->vscal.p, 0, 2 * sizeof(int64_t), s));
+    VertexParams p{};
+    const bool dev = res->mem == HT_DEVICE;
+    p.peaks = dev ? res->peaks : ctx->peaks.p;
+    p.n_peaks = dev ? res->counts : ctx->d_scal + 6;
+    p.peak_cap = res->peak_cap;
+    p.n_events = (int32_t)ne;
+    p.cphi = ctx->d_cphi;
+    p.sphi = ctx->d_sphi;
+    p.d0 = ctx->d_dtab;
+    p.nx = vg->n_x;
+    p.ny = vg->n_y;
+    p.xmin = (double)vg->x_min;
+    p.xmax = (double)vg->x_max;
+    p.ymin = (double)vg->y_min;
+    p.ymax = (double)vg->y_max;
+    p.acc = ctx->vacc.p;
+    p.thr = threshold;
+    p.rowcnt = ctx->vrow.p;
+    p.rowbase = ctx->vbase.p;
+    p.cap = cap;
+    if (dev) {
+        p.out = out;
+    } else {
+        CU(ctx->vout.ensure(std::max<int64_t>(cap, 1), nullptr));
+        p.out = ctx->vout.p;
+    }
+    if (p.peak_cap > 0 && (dev || res->counts[0] > 0)) CU(launch_vertex_vote(p, s));
+    CU(launch_vertex_rows(p, false, s));
+    ScanRange r{};
+    r.in = ctx->vrow.p;
+    r.out = ctx->vbase.p;
+    r.lo = 0;
+    r.hi = rows;
+    r.cap = rows;
+    r.base_dev = ctx->vscal.p + 0;
+    r.total = ctx->vscal.p + 1;
+    r.write_end = 1;
+    CU(launch_scan(r, ctx->scratch.p, s));
+    CU(launch_vertex_rows(p, true, s));
+    if (dev) {
+        CU(cudaMemcpyAsync(count, ctx->vscal.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        return HT_OK;
+    }
+    CU(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->vscal.p + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int64_t total = ctx->h_pinned[2];
+    *count = total;
+    const int64_t ncopy = std::min(total, cap);
+    if (ncopy > 0) {
+        CU(cudaMemcpyAsync(out, ctx->vout.p, ncopy * sizeof(ht_vertex), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    if (total > cap) return fail(ctx, HT_ERR_OVERFLOW, "%lld vertices, cap %lld", (long long)total, (long long)cap);
     return HT_OK;
 }
 

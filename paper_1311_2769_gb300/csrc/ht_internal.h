@@ -139,6 +139,26 @@ struct FitParams {
     int32_t nk;
 };
 cudaError_t launch_fit(const FitParams& p, cudaStream_t s);
+// second Hough transform for displaced vertices (ht_vertex.cu)
+struct VertexParams {
+    const ht_peak* peaks;
+    const int64_t* n_peaks;   // device scalar: the true peak count
+    int64_t peak_cap;
+    int32_t n_events;
+    const float* cphi;
+    const float* sphi;
+    const float4* d0;         // the first grid's d0 table (x = d0_j)
+    int32_t nx, ny;
+    double xmin, xmax, ymin, ymax;
+    uint32_t* acc;            // [n_events][nx][ny]
+    uint32_t thr;
+    int32_t* rowcnt;          // [n_events * nx] vertices per x row
+    const int64_t* rowbase;   // [n_events * nx] first output slot of each row
+    ht_vertex* out;
+    int64_t cap;
+};
+cudaError_t launch_vertex_vote(const VertexParams& p, cudaStream_t s);
+cudaError_t launch_vertex_rows(const VertexParams& p, bool emit, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
 
 }  // namespace ht

@@ -51,10 +51,11 @@ HT_MODE_PLAIN = 1
 EXPORTS = ("ht_create", "ht_destroy", "ht_set_option", "ht_get_option", "ht_vote", "ht_peaks",
            "ht_associate", "ht_process", "ht_get_accumulator", "ht_get_tables", "ht_sync",
            "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_peaks_noalloc", "ht_check_rcp", "ht_strerror", "ht_last_error",
-           "ht_fit")
+           "ht_fit", "ht_vertices")
 
 PEAK_DTYPE = np.dtype([("event", np.int32), ("i_phi", np.int32), ("i_d0", np.int32),
                        ("i_kappa", np.int32), ("votes", np.uint32)])
+VERTEX_DTYPE = np.dtype([("event", np.int32), ("i_x", np.int32), ("i_y", np.int32), ("votes", np.uint32)])
 TRACK_DTYPE = np.dtype([("status", np.int32), ("n_hits", np.int32), ("cos_phi0", np.float64),
                         ("sin_phi0", np.float64), ("d0", np.float64), ("kappa", np.float64),
                         ("chi2", np.float64)])
@@ -118,6 +119,7 @@ def load() -> ctypes.CDLL:
         "ht_check_rcp": [u32, u32, P],
         "ht_peaks_noalloc": [P, P, i32, u32, P, i64, P, P],
         "ht_fit": [P, P, P, i64, P],
+        "ht_vertices": [P, P, P, u32, P, i64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -374,6 +376,43 @@ def ht_fit(ctx, results, cap=None, stream=None):
     return out
 
 
+class HtVGrid(ctypes.Structure):
+    _fields_ = [("n_x", ctypes.c_int32), ("n_y", ctypes.c_int32), ("x_min", ctypes.c_float),
+                ("x_max", ctypes.c_float), ("y_min", ctypes.c_float), ("y_max", ctypes.c_float)]
+
+
+def ht_vertices(ctx, vg, results, threshold, cap=None, stream=None):
+    """Second Hough transform of the candidates in `results` (see ht.h).
+    Host results: (VERTEX_DTYPE array, true count).  Device results: (CUDA
+    uint8 tensor of cap * 16 bytes, CUDA int64 count tensor)."""
+    v = HtVGrid(int(vg.n_x), int(vg.n_y), float(vg.x_min), float(vg.x_max), float(vg.y_min), float(vg.y_max))
+    cap = 1 << 16 if cap is None else int(cap)
+    lib = load()
+    if isinstance(results.counts, np.ndarray):
+        while True:
+            out = np.zeros(max(cap, 1), VERTEX_DTYPE)
+            n = ctypes.c_int64()
+            st = lib.ht_vertices(ctx, ctypes.byref(v), ctypes.byref(results.struct), int(threshold), out.ctypes.data,
+                                 cap, ctypes.byref(n), _stream_ptr(stream))
+            if st == HT_ERR_OVERFLOW and n.value > cap:
+                cap = int(n.value)
+                continue
+            _check(st, ctx)
+            return out[: n.value].copy(), int(n.value)
+    import torch
+    dev = results.counts.device
+    out = torch.zeros(max(cap, 1) * VERTEX_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check(lib.ht_vertices(ctx, ctypes.byref(v), ctypes.byref(results.struct), int(threshold), _ptr(out), cap,
+                           _ptr(cnt), _stream_ptr(stream)), ctx)
+    return out, cnt
+
+
+def vertices_host(t, n):
+    """The first n vertices of a device vertex buffer as a VERTEX_DTYPE array."""
+    return np.frombuffer(t.cpu().numpy().tobytes(), VERTEX_DTYPE)[: int(n)].copy()
+
+
 def tracks_host(t, n):
     """The first n fits of a device fit buffer as a TRACK_DTYPE array."""
     return np.frombuffer(t.cpu().numpy().tobytes(), TRACK_DTYPE)[: int(n)].copy()
@@ -442,3 +481,6 @@ class Context:
 
     def fit(self, results, cap=None, stream=None):
         return ht_fit(self.handle, results, cap, stream)
+
+    def vertices(self, vg, results, threshold, cap=None, stream=None):
+        return ht_vertices(self.handle, vg, results, threshold, cap, stream)
