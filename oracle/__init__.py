@@ -79,6 +79,9 @@ def lib():
             "hto_fit_row": (None, [G, P, P, P, i64, i32, P]),
             "hto_vertex_vote": (None, [G, ctypes.POINTER(VGrid), P, i64, i32, P]),
             "hto_vertex_peaks": (i64, [ctypes.POINTER(VGrid), P, i32, u32, P, i64]),
+            "hto_line_bin": (i32, [G, f, f, i32]),
+            "hto_vote_line": (None, [G, P, P, P, i32, P]),
+            "hto_associate_line": (i64, [G, P, P, P, P, i64, i32, P, P, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -340,4 +343,37 @@ def vertex_peaks(v, acc, threshold) -> np.ndarray:
         n = lib().hto_vertex_peaks(ctypes.byref(vs), _ptr(acc), acc.shape[0], int(threshold), _ptr(out), cap)
         if n <= cap:
             return out[:n].copy()
+        cap = n
+
+
+# ---- straight displaced tracks (kappa = 0) -----------------------------------
+
+def line_bin(g, x, y, i) -> int:
+    return int(lib().hto_line_bin(ctypes.byref(grid_struct(g)), float(x), float(y), int(i)))
+
+
+def vote_line(g, x, y, event_offsets=None) -> np.ndarray:
+    """Line-vote accumulators [n_events, n_phi, n_d0, 1] uint32 (grid with n_kappa = 1)."""
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    offs = _offs(event_offsets, x.shape[0])
+    ne = offs.shape[0] - 1
+    acc = np.empty((ne, gs.n_phi, gs.n_d0, 1), dtype=np.uint32)
+    lib().hto_vote_line(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(offs), ne, _ptr(acc))
+    return acc
+
+
+def associate_line(g, x, y, event_offsets, pk, window):
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    offs = _offs(event_offsets, x.shape[0])
+    pk = np.ascontiguousarray(pk, dtype=PEAK_DTYPE)
+    po = np.empty(pk.shape[0] + 1, np.int64)
+    cap = 1 << 16
+    while True:
+        hi = np.empty(cap, np.int32)
+        n = lib().hto_associate_line(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(offs), _ptr(pk), pk.shape[0],
+                                     int(window), _ptr(po), _ptr(hi), cap)
+        if n <= cap:
+            return po, hi[:n].copy()
         cap = n

@@ -649,3 +649,72 @@ int64_t hto_vertex_peaks(const hto_vgrid *v, const uint32_t *acc, int32_t n_even
     }
     return n;
 }
+
+/* ---- straight displaced tracks (the paper's kappa = 0 model) --------------
+ *
+ * Section 3's implementation of the paper used two-parameter models; the
+ * straight displaced one is the line through the perigee d0 n with
+ * direction t, so a hit (x, y) lies on it when d0 = q = y cos phi0 - x sin phi0.
+ * Line voting: on a grid with a single kappa bin, each hit votes, for every
+ * phi0 row, in the d0 bin of q: floor((q - d0_min) n_d0 / (d0_max - d0_min))
+ * when that lies in [0, n_d0) (binary64, in this order: the two products of
+ * float values are exact, so q is rounded once).  It joins peak (i, j, 0)
+ * when its d0 bin in row i lies within `window` of j.
+ */
+static int32_t line_bin(const hto_grid *g, float xf, float yf, float cf, float sf)
+{
+    double q = ((double)yf * (double)cf) - ((double)xf * (double)sf);
+    double t = (q - (double)g->d0_min) * ((double)g->n_d0 / ((double)g->d0_max - (double)g->d0_min));
+    if (!(t >= 0.0 && t < (double)g->n_d0))
+        return -1;
+    return (int32_t)t;
+}
+
+int32_t hto_line_bin(const hto_grid *g, float x, float y, int32_t i)
+{
+    double phi = ((double)i + 0.5) * (2.0 * kPi / (double)g->n_phi);
+    return line_bin(g, x, y, (float)cos(phi), (float)sin(phi));
+}
+
+void hto_vote_line(const hto_grid *g, const float *x, const float *y, const int32_t *event_offsets,
+                   int32_t n_events, uint32_t *acc)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    const int64_t cells = (int64_t)g->n_phi * g->n_d0;
+    for (int32_t e = 0; e < n_events; ++e) {
+        uint32_t *a1 = acc + (int64_t)e * cells;
+        memset(a1, 0, sizeof(uint32_t) * (size_t)cells);
+        for (int64_t h = event_offsets[e]; h < event_offsets[e + 1]; ++h)
+            for (int32_t i = 0; i < g->n_phi; ++i) {
+                int32_t j = line_bin(g, x[h], y[h], c[i], s[i]);
+                if (j >= 0)
+                    a1[(int64_t)i * g->n_d0 + j] += 1u;
+            }
+    }
+    free(c); free(s); free(d);
+}
+
+int64_t hto_associate_line(const hto_grid *g, const float *x, const float *y, const int32_t *event_offsets,
+                           const hto_peak *peaks, int64_t n_peaks, int32_t window, int64_t *peak_offsets,
+                           int32_t *hit_idx, int64_t cap)
+{
+    float *c, *s, *d;
+    tables_alloc(g, &c, &s, &d);
+    int64_t n = 0;
+    peak_offsets[0] = 0;
+    for (int64_t p = 0; p < n_peaks; ++p) {
+        const hto_peak *pk = &peaks[p];
+        for (int64_t h = event_offsets[pk->event]; h < event_offsets[pk->event + 1]; ++h) {
+            int32_t j = line_bin(g, x[h], y[h], c[pk->i_phi], s[pk->i_phi]);
+            if (j >= 0 && abs(j - pk->i_d0) <= window) {
+                if (n < cap)
+                    hit_idx[n] = (int32_t)h;
+                ++n;
+            }
+        }
+        peak_offsets[p + 1] = n;
+    }
+    free(c); free(s); free(d);
+    return n;
+}

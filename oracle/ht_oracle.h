@@ -166,6 +166,17 @@ void hto_vertex_vote(const hto_grid *g, const hto_vgrid *v, const hto_peak *peak
 int64_t hto_vertex_peaks(const hto_vgrid *v, const uint32_t *acc, int32_t n_events, uint32_t threshold,
                          hto_vertex *out, int64_t cap);
 
+/* ---- straight displaced tracks (kappa = 0) --------------------------------
+ * On a grid with n_kappa = 1, each hit votes in every phi0 row for the d0 bin
+ * of q = y cos phi0 - x sin phi0 (binary64); it joins peak (i, j, 0) when its
+ * d0 bin in row i lies within `window` of j. */
+int32_t hto_line_bin(const hto_grid *g, float x, float y, int32_t i);
+void hto_vote_line(const hto_grid *g, const float *x, const float *y, const int32_t *event_offsets,
+                   int32_t n_events, uint32_t *acc);
+int64_t hto_associate_line(const hto_grid *g, const float *x, const float *y, const int32_t *event_offsets,
+                           const hto_peak *peaks, int64_t n_peaks, int32_t window, int64_t *peak_offsets,
+                           int32_t *hit_idx, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif
