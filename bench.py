@@ -243,9 +243,14 @@ def vertex_report(dev, n_jets=64, n_batch=512):
             ("batch_4096_lognormal", synth.generate(synth.WORKLOADS[WORKLOAD], n_events=n_batch),
              synth.WORKLOADS[WORKLOAD].grid, synth.WORKLOADS[WORKLOAD].threshold, 40)):
         ctx = ht.Context(g, synth.LAYERS_13)
+        if name == "displaced_jets":  # straight tracks: the paper's kappa = 0 model
+            ctx.set_option(ht.HT_OPT_VOTE_MODE, ht.HT_VOTE_LINE)
+            ctx.set_option(ht.HT_OPT_PHASE_TIMING, 1)
         res = ht.Results(b.n_events * 20000 + 4096, b.n_events * 800000 + 65536, device=dev)
-        ctx.process(ht.Hits.from_batch(b, device=dev), thr, 1, res)
-        ctx.sync()
+        for _ in range(2):
+            ctx.process(ht.Hits.from_batch(b, device=dev), thr, 1, res)
+            ctx.sync()
+        step = ctx.phase_times()[2] if name == "displaced_jets" else None
         ms = []
         s = torch.cuda.current_stream()
         for _ in range(3):
@@ -259,6 +264,8 @@ def vertex_report(dev, n_jets=64, n_batch=512):
         n = int(cnt.item())
         row = {"events": b.n_events, "candidates": int(res.counts[0].item()), "vertex_threshold": vthr,
                "ms": float(np.median(ms)), "vertices": n}
+        if step is not None:
+            row["line_vote_step_ms"] = step
         if name == "displaced_jets":
             got = ht.vertices_host(vo, min(n, 1 << 20))
             found = 0

@@ -136,7 +136,7 @@ typedef struct {
                                       bands; same results.  Default 3; no effect when the kappa
                                       range does not contain 0. */
 
-#define HT_OPT_VOTE_MODE 13        /* HT_VOTE_POINT (default) or HT_VOTE_RANGE */
+#define HT_OPT_VOTE_MODE 13        /* HT_VOTE_POINT (default), HT_VOTE_RANGE or HT_VOTE_LINE */
 #define HT_OPT_ASSOC_CURSORS 14    /* association row cursors per warp, a multiple of 32 (0 = auto:
                                       as many as fit 9 KB of shared memory per warp, 256..1024);
                                       a column block with more peaks is walked once per block of
@@ -155,6 +155,13 @@ typedef struct {
  * the point vote. */
 #define HT_VOTE_POINT 0
 #define HT_VOTE_RANGE 1
+/* HT_VOTE_LINE: the paper's straight displaced model (kappa = 0), on a grid
+ * with n_kappa = 1: each hit votes, in every phi0 row, for the d0 bin of
+ * q = y cos phi_i - x sin phi_i, floor((q - d0_min) n_d0 / (d0_max - d0_min))
+ * in binary64 (the two products of float values are exact); it joins peak
+ * (i, j, 0) when its d0 bin in row i lies within `window` of j.  Peaks are
+ * the local maxima of the [n_phi][n_d0] accumulator by the usual rule. */
+#define HT_VOTE_LINE 2
 
 #define HT_MODE_BATCHED 0 /* one persistent launch per kernel over all (event, tile) items */
 #define HT_MODE_PLAIN 1   /* one launch sequence per event */

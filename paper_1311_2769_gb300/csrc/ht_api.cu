@@ -74,6 +74,10 @@ struct ht_ctx {
     int64_t cells = 0;
     int64_t cols_per_event = 0;
     int nkw = 0;
+    // peak geometry: the accumulator as the peak and association stages see
+    // it, [phi][d0][kappa], or [phi][1][d0] for line voting (same memory)
+    int pnd = 0, pnk = 0;
+    KConsts Kp{};
 
     // options
     int mode = HT_MODE_BATCHED;
@@ -296,11 +300,12 @@ int resolve_tiles(ht_ctx* ctx) {
             }
     }
     int thr = ctx->threads > 0 ? ctx->threads : 256;
-    const bool range = ctx->vote_mode == HT_VOTE_RANGE;
-    // bands bound point votes only: range voting sweeps every cell
+    const bool line = ctx->vote_mode == HT_VOTE_LINE;
+    const bool range = ctx->vote_mode == HT_VOTE_RANGE || line;
+    // bands bound point votes only: range and line voting sweep every cell
     const bool band = !range && (ctx->prune & 1) && ctx->K.band_ok;
     ctx->a_band = !range && (ctx->prune & 2) && ctx->K.band_ok;
-    const int variant = range ? 2 : (band ? 1 : 0);
+    const int variant = ctx->vote_mode == HT_VOTE_RANGE ? 2 : (band ? 1 : 0);
     const int smem = vote_smem_bytes(tp, td, nk, thr, variant);
     if (smem > 227 * 1024)
         return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d needs %d B of shared memory", tp, td, nk, smem);
@@ -326,17 +331,19 @@ int resolve_tiles(ht_ctx* ctx) {
     constexpr size_t kWarpBudget = 9216;
     const int athr = std::min(thr, 256);
     if (range) {
-        // range association: one row x up to 32 d0 columns per item
-        int atd = std::min(ctx->atile_d > 0 ? ctx->atile_d : 32, std::min(nd, 32));
-        while (atd > 1 && assoc_range_warp_smem(atd, nk, 256) > kWarpBudget) atd = (atd + 1) / 2;
-        const size_t fixed = assoc_range_warp_smem(atd, nk, 0);
+        // range (and line) association: one row x up to 32 columns per item
+        // of the peak geometry (line voting: one column of n_d0 bins)
+        const int gnd = ctx->pnd, gnk = ctx->pnk;
+        int atd = std::min(ctx->atile_d > 0 ? ctx->atile_d : 32, std::min(gnd, 32));
+        while (atd > 1 && assoc_range_warp_smem(atd, gnk, 256) > kWarpBudget) atd = (atd + 1) / 2;
+        const size_t fixed = assoc_range_warp_smem(atd, gnk, 0);
         int cap = fixed + 4 * 256 <= kWarpBudget ? (int)((kWarpBudget - fixed) / 4) & ~31 : 256;
         cap = ctx->acap > 0 ? ctx->acap : std::min(cap, 1024);
-        const size_t wbytes = assoc_range_warp_smem(atd, nk, cap);
+        const size_t wbytes = assoc_range_warp_smem(atd, gnk, cap);
         const int asmem = (int)(wbytes * (athr / 32));
         if (asmem > 227 * 1024) return fail(ctx, HT_ERR_INVALID_ARG, "association item does not fit shared memory");
         int ablocks = 0;
-        CU(assoc_range_prepare(nk, asmem, athr, &ablocks));
+        CU(assoc_range_prepare(gnk, asmem, athr, &ablocks, line));
         if (ablocks < 1) return fail(ctx, HT_ERR_INVALID_ARG, "association kernel cannot launch");
         ctx->a_tile_phi = 1;
         ctx->a_tile_d = atd;
@@ -490,6 +497,12 @@ VoteParams vote_params(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent)
 int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStream_t s) {
     if (ne <= 0) return HT_OK;
     VoteParams p = vote_params(ctx, event0, ne, persistent);
+    if (ctx->vote_mode == HT_VOTE_LINE) {
+        if (persistent) CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
+        CU(cudaMemsetAsync(ctx->acc.p, 0, (size_t)ne * ctx->cells * sizeof(uint32_t), s));
+        CU(launch_vote_line(p, (double)ctx->grid.d0_min, (double)ctx->grid.d0_max, s));
+        return HT_OK;
+    }
     if (persistent) {
         CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
         CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), s));
@@ -510,9 +523,10 @@ PeakParams peak_params(ht_ctx* ctx, int32_t event0, int32_t ne, uint32_t thr, ht
     p.event0 = event0;
     p.thr = thr;
     p.nphi = ctx->grid.n_phi;
-    p.nd = ctx->grid.n_d0;
-    p.nk = ctx->grid.n_kappa;
+    p.nd = ctx->pnd;
+    p.nk = ctx->pnk;
     p.nkw = ctx->nkw;
+    p.line = ctx->vote_mode == HT_VOTE_LINE ? 1 : 0;
     p.mask = ctx->mask.p;
     p.wpre = ctx->wpre.p;
     p.npk = ctx->npk.p;
@@ -571,10 +585,15 @@ int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, co
     a.ecos = ctx->d_ecos;
     a.esin = ctx->d_esin;
     a.edtab = ctx->d_edtab;
-    a.K = ctx->K;
+    a.K = ctx->Kp;
     a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+    if (ctx->vote_mode == HT_VOTE_LINE) {
+        a.line_nd = ctx->grid.n_d0;
+        a.line_d0min = (double)ctx->grid.d0_min;
+        a.line_d0max = (double)ctx->grid.d0_max;
+    }
     const int64_t items = (int64_t)ne * ((ctx->grid.n_phi + ctx->a_tile_phi - 1) / ctx->a_tile_phi) *
-                          ((ctx->grid.n_d0 + ctx->a_tile_d - 1) / ctx->a_tile_d);
+                          ((ctx->pnd + ctx->a_tile_d - 1) / ctx->a_tile_d);
     const int warps = ctx->a_threads / 32;
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>((items + warps - 1) / warps, (int64_t)ctx->sms * ctx->a_blocks_per_sm));
@@ -592,9 +611,10 @@ int mark(ht_ctx* ctx, int which, cudaStream_t s);
 int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* order, int64_t peak_cap,
                     int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, bool timed,
                     cudaStream_t s) {
-    const bool range = ctx->vote_mode == HT_VOTE_RANGE;
+    const bool range = ctx->vote_mode != HT_VOTE_POINT;
     if (range) {
-        // row lengths by a counting pass (window sums over-count range votes)
+        // row lengths by a counting pass (window sums over-count range votes;
+        // line votes run along d0, across the window sums' kappa axis)
         AssocParams c{};
         c.peak_offsets = peak_offsets;
         c.peak_cap = peak_cap;
@@ -671,7 +691,7 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
         if (st) return st;
         if (single && (st = mark(ctx, 1, s))) return st;
         // range voting counts rows in the association (window sums over-count)
-        PeakParams pp = peak_params(ctx, e0, ne, thr, peaks, peak_cap, ctx->vote_mode == HT_VOTE_RANGE ? -1 : window);
+        PeakParams pp = peak_params(ctx, e0, ne, thr, peaks, peak_cap, ctx->vote_mode != HT_VOTE_POINT ? -1 : window);
         st = run_detect_scan(ctx, pp, s);
         if (st) return st;
         CU(launch_emit(pp, s));
@@ -679,7 +699,7 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
                              window, single, s);
         if (st) return st;
         if (single && (st = mark(ctx, 2, s))) return st;
-        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode == HT_VOTE_RANGE ? 1 : 0);
+        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode != HT_VOTE_POINT ? 1 : 0);
     }
     if (single && (st = mark(ctx, 3, s))) return st;
     if (ctx->c_events == 0 && peak_offsets && peak_cap >= 0)
@@ -744,6 +764,9 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
     ctx->cells = (int64_t)grid->n_phi * grid->n_d0 * grid->n_kappa;
     ctx->cols_per_event = (int64_t)grid->n_phi * grid->n_d0;
     ctx->nkw = (grid->n_kappa + 31) / 32;
+    ctx->pnd = grid->n_d0;
+    ctx->pnk = grid->n_kappa;
+    ctx->Kp = ctx->K;
     std::vector<float4> dt(grid->n_d0);
     for (int j = 0; j < grid->n_d0; ++j) {
         const float d = ctx->h_d0[j];
@@ -881,12 +904,28 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
                 return fail(ctx, HT_ERR_INVALID_ARG, "association cursors must be 0 or a multiple of 32 up to 65536");
             ctx->acap = (int)value;
             break;
-        case HT_OPT_VOTE_MODE:
-            if (value != HT_VOTE_POINT && value != HT_VOTE_RANGE)
-                return fail(ctx, HT_ERR_INVALID_ARG, "vote mode must be HT_VOTE_POINT or HT_VOTE_RANGE");
+        case HT_OPT_VOTE_MODE: {
+            if (value != HT_VOTE_POINT && value != HT_VOTE_RANGE && value != HT_VOTE_LINE)
+                return fail(ctx, HT_ERR_INVALID_ARG, "vote mode must be HT_VOTE_POINT, HT_VOTE_RANGE or HT_VOTE_LINE");
+            if (value == HT_VOTE_LINE && ctx->grid.n_kappa != 1)
+                return fail(ctx, HT_ERR_INVALID_ARG, "line voting needs a grid with n_kappa = 1");
+            const bool line = value == HT_VOTE_LINE;
+            const int pnd = line ? 1 : ctx->grid.n_d0, pnk = line ? ctx->grid.n_d0 : ctx->grid.n_kappa;
+            if (detect_smem(ctx->grid.n_phi, pnd, pnk) > 227 * 1024)
+                return fail(ctx, HT_ERR_INVALID_ARG, "peak detection tile does not fit shared memory");
+            CU(detect_prepare(ctx->grid.n_phi, pnd, pnk));
             ctx->vote_mode = (int)value;
-            ctx->have_peaks = false;
+            ctx->pnd = pnd;
+            ctx->pnk = pnk;
+            ctx->nkw = (pnk + 31) / 32;
+            ctx->cols_per_event = (int64_t)ctx->grid.n_phi * pnd;
+            ctx->Kp = ctx->K;
+            ctx->Kp.nd = pnd;
+            ctx->Kp.nk = pnk;
+            ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
+            ++ctx->gen;
             break;
+        }
         case HT_OPT_PHASE_TIMING:
             if (value && !ctx->tev[0])
                 for (auto& e : ctx->tev) CU(cudaEventCreate(&e));
@@ -995,7 +1034,7 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     CU(cudaMemsetAsync(ctx->d_scal, 0, 8 * sizeof(int64_t), s));
     ctx->h_pinned[0] = np;
     CU(cudaMemcpyAsync(ctx->d_scal + 0, ctx->h_pinned, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    if (ctx->vote_mode == HT_VOTE_RANGE) {
+    if (ctx->vote_mode != HT_VOTE_POINT) {
         AssocParams c{};
         c.peak_offsets = ctx->peakoff.p;
         c.peak_cap = np;
@@ -1029,7 +1068,7 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     a.hit_idx = ctx->hitidx.p;
     a.pair_cap = total;
     a.window = window;
-    const int st = launch_assoc_ctx(ctx, a, 0, ctx->c_events, nullptr, ctx->vote_mode == HT_VOTE_RANGE ? 2 : 0, s);
+    const int st = launch_assoc_ctx(ctx, a, 0, ctx->c_events, nullptr, ctx->vote_mode != HT_VOTE_POINT ? 2 : 0, s);
     if (st) return st;
     CU(cudaMemcpyAsync(peak_offsets, ctx->peakoff.p, (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     const int64_t ncopy = std::min(total, cap);

@@ -48,6 +48,7 @@ struct PeakParams {
     int32_t window;         // < 0: no pair counts
     int32_t* paircnt;       // [peak_cap]
     int64_t* extra_pairs;   // pairs of peaks beyond peak_cap (device scalar) or nullptr
+    int32_t line;           // 1: line voting's [phi][1][d0] view, emitted as (phi, d0, 0)
 };
 
 struct AssocParams {
@@ -76,6 +77,8 @@ struct AssocParams {
     const float4* edtab;
     int32_t* paircnt;       // range counting pass: row lengths of stored peaks
     int64_t* extra_pairs;   // range counting pass: pairs of peaks past the cap (device scalar)
+    int32_t line_nd;        // line voting (K holds the [phi][1][d0] view): n_d0, 0 otherwise
+    double line_d0min, line_d0max;
     const float* cphi;
     const float* sphi;
     const float4* dtab;
@@ -123,7 +126,8 @@ size_t assoc_warp_smem(int rows, int wd, int nk, int cap);
 cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band, int threads, int* blocks_per_sm);
 cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int grid, cudaStream_t s);
 size_t assoc_range_warp_smem(int wd, int nk, int cap);
-cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm);
+cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm, bool line = false);
+cudaError_t launch_vote_line(const VoteParams& p, double d0min, double d0max, cudaStream_t s);
 cudaError_t launch_assoc_range(const AssocParams& p, bool count, int threads, int grid, cudaStream_t s);
 // circle fit of the stored candidates' rows (ht_fit.cu)
 struct FitParams {

@@ -470,6 +470,33 @@ __global__ void __launch_bounds__(256, 3) vote_range_kernel(const VoteParams p) 
 }
 
 // ---------------------------------------------------------------------------
+// line vote (the kappa = 0 model): every hit, every phi0 row, one d0 bin
+// ---------------------------------------------------------------------------
+// q = y cos phi_i - x sin phi_i from exact binary64 products of the float
+// inputs (rounded once), its bin floor((q - d0_min) n_d0 / (d0_max - d0_min))
+// in binary64; a block per event, global atomics into the zeroed
+// accumulator [phi][d0] (one kappa bin).
+__global__ void vote_line_kernel(const VoteParams p, double d0min, double d0max) {
+    const int nphi = p.K.nphi, nd = p.K.nd;
+    const double ndr = (double)nd;
+    const double scale = __ddiv_rn(ndr, __dsub_rn(d0max, d0min));
+    for (int e = blockIdx.x; e < p.n_events; e += gridDim.x) {
+        const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
+        const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
+        uint32_t* a1 = p.acc + (int64_t)e * p.cells;
+        const int64_t work = (he - hb) * nphi;
+        for (int64_t t = threadIdx.x; t < work; t += blockDim.x) {
+            const int64_t h = hb + t / nphi;
+            const int i = (int)(t - (t / nphi) * nphi);
+            const double q = __dsub_rn(__dmul_rn((double)p.y[h], (double)p.cphi[i]),
+                                       __dmul_rn((double)p.x[h], (double)p.sphi[i]));
+            const double u = __dmul_rn(__dsub_rn(q, d0min), scale);
+            if (u >= 0.0 && u < ndr) atomicAdd(a1 + (int64_t)i * nd + (int)u, 1u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // input validation (device-resident batches)
 // bit 1: non-finite or |coordinate| > 1e4; bit 2: layer out of range; bit 4: offsets
 // ---------------------------------------------------------------------------
@@ -666,8 +693,8 @@ __global__ void emit_kernel(const PeakParams p) {
             ht_peak pk;
             pk.event = p.event0 + e;
             pk.i_phi = i;
-            pk.i_d0 = j;
-            pk.i_kappa = k;
+            pk.i_d0 = p.line ? k : j;  // line voting runs peaks on the [phi][1][d0] view
+            pk.i_kappa = p.line ? 0 : k;
             pk.votes = colp[k];
             p.peaks[pid] = pk;
             if (p.window >= 0) {
@@ -1227,7 +1254,7 @@ __device__ __forceinline__ void range_edge_codes(const AssocParams& p, float x, 
     }
 }
 
-template <int NK, bool COUNT>
+template <int NK, bool COUNT, bool LINE>
 __global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = NK ? NK : p.K.nk;
@@ -1281,7 +1308,8 @@ __global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p
             S.mask[v] = ok ? p.mask[col * nkw + wd] : 0u;
             S.lpre[v] = ok ? (int)(p.colbase[col] - P0) + p.wpre[col * nkw + wd] : 0;
         }
-        for (int v = lane; v <= nj; v += 32) S.dte[v] = p.edtab[j0 + v];
+        if (!LINE)
+            for (int v = lane; v <= nj; v += 32) S.dte[v] = p.edtab[j0 + v];
         __syncwarp();
         for (int v = lane; v < WD * nkw; v += 32) {
             const int wd = v - (v / nkw) * nkw;
@@ -1292,7 +1320,11 @@ __global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p
             S.nearb[v] = nb;
         }
         const int i1 = (i0 + 1) % p.K.nphi;
-        const float ce[2] = {p.ecos[i0], p.ecos[i1]}, se[2] = {p.esin[i0], p.esin[i1]};
+        const float ce[2] = {LINE ? 0.0f : p.ecos[i0], LINE ? 0.0f : p.ecos[i1]};
+        const float se[2] = {LINE ? 0.0f : p.esin[i0], LINE ? 0.0f : p.esin[i1]};
+        // line voting: the row's centre tables and the d0 binning
+        const double lc = LINE ? (double)p.cphi[i0] : 0.0, ls = LINE ? (double)p.sphi[i0] : 0.0;
+        const double lscale = LINE ? __ddiv_rn((double)p.line_nd, __dsub_rn(p.line_d0max, p.line_d0min)) : 0.0;
         const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
         const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
         const int64_t eh = he - hb > 1 ? he - hb : 1;
@@ -1317,24 +1349,37 @@ __global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p
                     qe[m] = q_of(x, y, ce[m], se[m]);
                     qse[m] = qe[m] * S2;
                 }
+                int jline = -1;
+                if (LINE && valid) {
+                    const double q = __dsub_rn(__dmul_rn((double)y, lc), __dmul_rn((double)x, ls));
+                    const double u = __dmul_rn(__dsub_rn(q, p.line_d0min), lscale);
+                    if (u >= 0.0 && u < (double)p.line_nd) jline = (int)u;
+                }
                 int left[2], right[2];
                 int ln = -2;  // d0 edge whose codes are in `right`
                 unsigned jm = jmask;
                 while (jm) {
                     const int j = __ffs(jm) - 1;
                     jm &= jm - 1u;
-                    if (j == ln) {
-                        left[0] = right[0];
-                        left[1] = right[1];
+                    int a, b;
+                    bool def;
+                    if (LINE) {  // the row's single column: the hit's d0 bin
+                        a = b = jline;
+                        def = jline >= 0;
                     } else {
-                        range_edge_codes(p, x, y, hf, qe, qse, ce, se, S.dte[j], valid, nk, left);
+                        if (j == ln) {
+                            left[0] = right[0];
+                            left[1] = right[1];
+                        } else {
+                            range_edge_codes(p, x, y, hf, qe, qse, ce, se, S.dte[j], valid, nk, left);
+                        }
+                        range_edge_codes(p, x, y, hf, qe, qse, ce, se, S.dte[j + 1], valid, nk, right);
+                        ln = j + 1;
+                        a = min(min(left[0], left[1]), min(right[0], right[1]));
+                        b = max(max(left[0], left[1]), max(right[0], right[1]));
+                        def = left[0] != kCodeUndef && left[1] != kCodeUndef && right[0] != kCodeUndef &&
+                              right[1] != kCodeUndef && b >= 0 && a < nk;
                     }
-                    range_edge_codes(p, x, y, hf, qe, qse, ce, se, S.dte[j + 1], valid, nk, right);
-                    ln = j + 1;
-                    const int a = min(min(left[0], left[1]), min(right[0], right[1]));
-                    const int b = max(max(left[0], left[1]), max(right[0], right[1]));
-                    const bool def = left[0] != kCodeUndef && left[1] != kCodeUndef && right[0] != kCodeUndef &&
-                                     right[1] != kCodeUndef && b >= 0 && a < nk;
                     const int lo = max(a, 0), hi = min(b, nk - 1);
                     // near-peak bins inside [lo, hi]
                     bool cand = false;
@@ -1655,10 +1700,13 @@ cudaError_t launch_assoc(const AssocParams& p, int tile_phi, int threads, int gr
 
 template <int N, bool C>
 static void* assoc_range_fn() {
-    return reinterpret_cast<void*>(assoc_range_kernel<N, C>);
+    return reinterpret_cast<void*>(assoc_range_kernel<N, C, false>);
 }
 
-static void* assoc_range_instance(int nk, bool count) {
+static void* assoc_range_instance(int nk, bool count, bool line = false) {
+    if (line)
+        return count ? reinterpret_cast<void*>(assoc_range_kernel<0, true, true>)
+                     : reinterpret_cast<void*>(assoc_range_kernel<0, false, true>);
     switch (nk) {
         case 64: return count ? assoc_range_fn<64, true>() : assoc_range_fn<64, false>();
         case 128: return count ? assoc_range_fn<128, true>() : assoc_range_fn<128, false>();
@@ -1670,10 +1718,10 @@ static void* assoc_range_instance(int nk, bool count) {
 
 size_t assoc_range_warp_smem(int wd, int nk, int cap) { return assoc_range_warp_bytes(wd, nk, cap); }
 
-cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm) {
+cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm, bool line) {
     int b[2] = {0, 0};
     for (int c = 0; c < 2; ++c) {
-        void* f = assoc_range_instance(nk, c != 0);
+        void* f = assoc_range_instance(nk, c != 0, line);
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[c], f, threads, smem);
@@ -1685,10 +1733,17 @@ cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_s
 
 cudaError_t launch_assoc_range(const AssocParams& p, bool count, int threads, int grid, cudaStream_t s) {
     if ((int64_t)p.n_events * p.K.nphi == 0) return cudaSuccess;
-    void* f = assoc_range_instance(p.K.nk, count);
+    void* f = assoc_range_instance(p.K.nk, count, p.line_nd > 0);
     const int smem = (int)(p.warp_bytes * (threads / 32));
     void* args[] = {const_cast<AssocParams*>(&p)};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s);
+}
+
+cudaError_t launch_vote_line(const VoteParams& p, double d0min, double d0max, cudaStream_t s) {
+    if (p.n_events <= 0) return cudaSuccess;
+    const int grid = p.n_events < 152 * 8 ? p.n_events : 152 * 8;
+    vote_line_kernel<<<grid, 256, 0, s>>>(p, d0min, d0max);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s) {

@@ -45,6 +45,7 @@ HT_OPT_VOTE_MODE = 13
 HT_OPT_ASSOC_CURSORS = 14
 HT_VOTE_POINT = 0
 HT_VOTE_RANGE = 1
+HT_VOTE_LINE = 2
 HT_MODE_BATCHED = 0
 HT_MODE_PLAIN = 1
 
