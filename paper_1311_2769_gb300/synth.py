@@ -158,10 +158,17 @@ class Batch:
 
 
 def concat(batches) -> Batch:
-    """Pack several batches into one (event order preserved)."""
+    """Pack several batches into one (event order preserved).  The layer
+    radii of the result are the longest of the batches' tables; every other
+    table must be a prefix of it, so that each hit's layer id stays valid."""
     batches = list(batches)
     if not batches:
         raise ValueError("concat needs at least one batch")
+    layer_r = max((np.asarray(b.layer_r, np.float32) for b in batches), key=len)
+    for b in batches:
+        lr = np.asarray(b.layer_r, np.float32)
+        if not np.array_equal(lr, layer_r[:len(lr)]):
+            raise ValueError("concat: layer radii differ between batches")
     offs = [0]
     for b in batches:
         base = offs[-1]
@@ -176,7 +183,7 @@ def concat(batches) -> Batch:
                  np.concatenate([b.y for b in batches]).astype(np.float32),
                  np.concatenate([b.z for b in batches]).astype(np.float32),
                  np.concatenate([b.layer for b in batches]).astype(np.int8),
-                 np.asarray(offs, dtype=np.int32), batches[0].layer_r, tt, tp)
+                 np.asarray(offs, dtype=np.int32), layer_r, tt, tp)
 
 
 def _draw_pt(rng, spec, n):
