@@ -82,6 +82,7 @@ def lib():
             "hto_line_bin": (i32, [G, f, f, i32]),
             "hto_vote_line": (None, [G, P, P, P, i32, P]),
             "hto_associate_line": (i64, [G, P, P, P, P, i64, i32, P, P, i64]),
+            "hto_merge": (i64, [G, P, P, P, i64, P, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -313,6 +314,25 @@ def fit_hits(g, x, y, i_kappa) -> np.void:
     out = np.zeros(1, TRACK_DTYPE)
     lib().hto_fit_row(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(idx), x.shape[0], int(i_kappa), _ptr(out))
     return out[0]
+
+
+MERGE_KEPT, MERGE_DUPLICATE, MERGE_BACKWARD, MERGE_UNFITTED = 1, 0, -1, -2
+
+
+def merge(g, x, y, pk, peak_offsets, hit_idx, fits, radius=2):
+    """Duplicate and mirror merging of fitted candidates: (state int32 per
+    candidate, number kept)."""
+    gs = grid_struct(g)
+    x, y = _f32(x), _f32(y)
+    pk = np.ascontiguousarray(pk, dtype=PEAK_DTYPE)
+    po = np.ascontiguousarray(peak_offsets, dtype=np.int64)
+    hi = np.ascontiguousarray(hit_idx, dtype=np.int32)
+    fits = np.ascontiguousarray(fits, dtype=TRACK_DTYPE)
+    assert fits.shape[0] == pk.shape[0] and po.shape[0] == pk.shape[0] + 1
+    state = np.zeros(pk.shape[0], np.int32)
+    kept = lib().hto_merge(ctypes.byref(gs), _ptr(x), _ptr(y), _ptr(pk), pk.shape[0], _ptr(po), _ptr(hi),
+                           _ptr(fits), int(radius), _ptr(state))
+    return state, int(kept)
 
 
 # ---- second Hough transform: displaced vertices ------------------------------

@@ -718,3 +718,77 @@ int64_t hto_associate_line(const hto_grid *g, const float *x, const float *y, co
     free(c); free(s); free(d);
     return n;
 }
+
+/* ---- duplicate and mirror merging of fitted candidates (second extension) --
+ *
+ * Section 3 hands the transform's candidates to a confirmation step.  Every
+ * track leaves two kinds of extra candidates: the mirror cell (phi0 + pi,
+ * -d0, -kappa), the same circle travelled the other way, and nearby cells
+ * that its hits also fill above threshold.  Reading used here, applied after
+ * the circle fit:
+ *  1. A candidate whose fit has status != 1 is UNFITTED.
+ *  2. A track leaves its perigee P = d0 n moving along t = (cos phi0,
+ *     sin phi0), so its hits lie ahead of P: (h - P).t > 0, and since
+ *     P.t = 0 this is h.t.  A fitted candidate is BACKWARD (the mirror of a
+ *     forward one) unless the sum over its row's hits, in row order, of
+ *     x cos phi0 + y sin phi0 (each term fl(fl(x c) + fl(y s)), summed in
+ *     binary64) is > 0.
+ *  3. A forward fitted candidate is a DUPLICATE when another forward fitted
+ *     candidate of the same event lies within `radius` cells of it in each
+ *     of phi0 (periodic), d0 and kappa and is better: more votes, or as many
+ *     and a smaller index.  Otherwise it is KEPT.
+ * Written as the definition: every pair of the event's candidates is
+ * compared (peaks must be grouped by event).  Returns the number kept.
+ */
+static int32_t phi_distance(int32_t a, int32_t b, int32_t n_phi)
+{
+    int32_t d = abs(a - b);
+    return d < n_phi - d ? d : n_phi - d;
+}
+
+int64_t hto_merge(const hto_grid *g, const float *x, const float *y, const hto_peak *peaks, int64_t n_peaks,
+                  const int64_t *peak_offsets, const int32_t *hit_idx, const hto_track *fits,
+                  int32_t radius, int32_t *state)
+{
+    for (int64_t p = 0; p < n_peaks; ++p) {
+        const hto_track *f = &fits[p];
+        if (f->status != 1) {
+            state[p] = HTO_MERGE_UNFITTED;
+            continue;
+        }
+        double t = 0.0;
+        for (int64_t q = peak_offsets[p]; q < peak_offsets[p + 1]; ++q) {
+            int32_t h = hit_idx[q];
+            t = t + (((double)x[h] * f->cos_phi0) + ((double)y[h] * f->sin_phi0));
+        }
+        state[p] = t > 0.0 ? HTO_MERGE_KEPT : HTO_MERGE_BACKWARD;
+    }
+    int64_t kept = 0;
+    int64_t lo = 0, hi = 0; /* [lo, hi): the candidates of p's event (peaks are grouped by event) */
+    for (int64_t p = 0; p < n_peaks; ++p) {
+        if (p == hi) {
+            lo = p;
+            for (hi = p; hi < n_peaks && peaks[hi].event == peaks[p].event; ++hi)
+                ;
+        }
+        if (state[p] != HTO_MERGE_KEPT && state[p] != HTO_MERGE_DUPLICATE)
+            continue;
+        const hto_peak *a = &peaks[p];
+        int dup = 0;
+        for (int64_t q = lo; q < hi && !dup; ++q) {
+            const hto_peak *b = &peaks[q];
+            if (q == p)
+                continue;
+            if (state[q] != HTO_MERGE_KEPT && state[q] != HTO_MERGE_DUPLICATE)
+                continue;
+            if (phi_distance(a->i_phi, b->i_phi, g->n_phi) > radius || abs(a->i_d0 - b->i_d0) > radius ||
+                abs(a->i_kappa - b->i_kappa) > radius)
+                continue;
+            if (b->votes > a->votes || (b->votes == a->votes && q < p))
+                dup = 1;
+        }
+        state[p] = dup ? HTO_MERGE_DUPLICATE : HTO_MERGE_KEPT;
+        kept += !dup;
+    }
+    return kept;
+}

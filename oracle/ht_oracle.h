@@ -177,6 +177,20 @@ int64_t hto_associate_line(const hto_grid *g, const float *x, const float *y, co
                            const hto_peak *peaks, int64_t n_peaks, int32_t window, int64_t *peak_offsets,
                            int32_t *hit_idx, int64_t cap);
 
+/* ---- duplicate and mirror merging ----------------------------------------
+ * After the fit: UNFITTED (status != 1); BACKWARD (the row's hits do not lie
+ * ahead of the perigee: the binary64 sum of x cos phi0 + y sin phi0 is not
+ * > 0); DUPLICATE when a better (more votes, then smaller index) forward
+ * fitted candidate of the same event lies within `radius` cells in each of
+ * phi0 (periodic), d0, kappa; else KEPT.  Returns the number kept. */
+#define HTO_MERGE_KEPT 1
+#define HTO_MERGE_DUPLICATE 0
+#define HTO_MERGE_BACKWARD (-1)
+#define HTO_MERGE_UNFITTED (-2)
+int64_t hto_merge(const hto_grid *g, const float *x, const float *y, const hto_peak *peaks, int64_t n_peaks,
+                  const int64_t *peak_offsets, const int32_t *hit_idx, const hto_track *fits,
+                  int32_t radius, int32_t *state);
+
 #ifdef __cplusplus
 }
 #endif
