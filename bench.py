@@ -417,7 +417,21 @@ def run_gpu(args):
     fitted = int((fits.view(torch.int32)[0::12][:n_fit] == 1).sum().item())  # status, every 48 bytes
     fit_info = {"ms": float(np.median(fit_ms)), "candidates": n_fit, "fitted": fitted,
                 "candidates_per_s": n_fit / (float(np.median(fit_ms)) / 1e3)}
-    del fits
+    # duplicate and mirror merging of those fits (radius 2; not in the step)
+    merge_ms = []
+    for _ in range(3):
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        state, kept = ctx.merge(res, fits, 2, stream=stream)
+        m1.record(stream)
+        m1.synchronize()
+        merge_ms.append(m0.elapsed_time(m1))
+    st = torch.bincount((state[:n_fit] + 2).to(torch.int64), minlength=4).cpu().numpy()
+    merge_info = {"ms": float(np.median(merge_ms)), "radius": 2, "kept": int(kept.item()),
+                  "duplicate": int(st[2]), "backward": int(st[1]), "unfitted": int(st[0]),
+                  "candidates_per_s": n_fit / (float(np.median(merge_ms)) / 1e3)}
+    del fits, state
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_events / (ms / 1e3), "ms_per_step": ms,
@@ -560,6 +574,7 @@ def run_gpu(args):
         "serving": serving,
         "range_vote": range_vote,
         "fit": fit_info,
+        "merge": merge_info,
         "vertex": vertex,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -249,6 +249,32 @@ typedef struct {
 } ht_track;
 int ht_fit(ht_ctx *ctx, const ht_results *res, ht_track *out, int64_t cap, void *stream);
 
+/* Duplicate and mirror merging of the fitted candidates of the last
+ * ht_process (Section 3's confirmation step; this library's reading, not a
+ * formula of the paper).  For each stored candidate c < min(n_peaks,
+ * peak_cap, cap), with fits[c] from ht_fit on the same `res`:
+ *   HT_MERGE_UNFITTED  fits[c].status != 1;
+ *   HT_MERGE_BACKWARD  its hits do not lie ahead of its perigee: the
+ *                      binary64 sum over its CSR row, in row order, of
+ *                      x cos phi0 + y sin phi0 is not > 0 (the mirror cell
+ *                      (phi0 + pi, -d0, -kappa) of a forward track);
+ *   HT_MERGE_DUPLICATE another forward fitted candidate of the same event
+ *                      lies within `radius` cells in phi0 (periodic), d0 and
+ *                      kappa and is better: more votes, or as many and a
+ *                      smaller index;
+ *   HT_MERGE_KEPT      otherwise.
+ * Radius 0 and 1 merge mirrors only (peaks are never neighbours).  fits[cap]
+ * and state[cap] (int32) and *n_kept (the number KEPT) live in res->mem:
+ * with device results the call is asynchronous on `stream`, with host
+ * results it synchronises.  0 <= radius <= 64, else HT_ERR_INVALID_ARG; no
+ * preceding ht_process: HT_ERR_STATE. */
+#define HT_MERGE_KEPT 1
+#define HT_MERGE_DUPLICATE 0
+#define HT_MERGE_BACKWARD (-1)
+#define HT_MERGE_UNFITTED (-2)
+int ht_merge(ht_ctx *ctx, const ht_results *res, const ht_track *fits, int32_t radius, int32_t *state,
+             int64_t cap, int64_t *n_kept, void *stream);
+
 /* Second Hough transform for displaced vertices (Section "Displaced vertex
  * identification": tracks from a common vertex (xv, yv) satisfy
  * d0 = yv cos phi0 - xv sin phi0, and a second transform of the first one's

@@ -129,6 +129,8 @@ struct ht_ctx {
     int32_t c_wave_events = 0;
     bool have_votes = false, have_peaks = false, have_results = false;
     DBuf<ht_track> fits;  // device staging of fits for host results
+    DBuf<int32_t> mstate;               // device staging of merge states for host results
+    DBuf<unsigned long long> mkept;     // merge: kept counter
     // second Hough transform: accumulators, per-row counts and bases, scalars, staging
     DBuf<uint32_t> vacc;
     DBuf<int32_t> vrow;
@@ -849,6 +851,8 @@ int ht_destroy(ht_ctx* ctx) {
     ctx->peakoff.release();
     ctx->hitidx.release();
     ctx->fits.release();
+    ctx->mstate.release();
+    ctx->mkept.release();
     ctx->vacc.release();
     ctx->vrow.release();
     ctx->vbase.release();
@@ -1263,6 +1267,61 @@ int ht_fit(ht_ctx* ctx, const ht_results* res, ht_track* out, int64_t cap, void*
     CU(launch_fit(p, s));
     CU(cudaMemcpyAsync(out, ctx->fits.p, n * sizeof(ht_track), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    return HT_OK;
+}
+
+int ht_merge(ht_ctx* ctx, const ht_results* res, const ht_track* fits, int32_t radius, int32_t* state,
+             int64_t cap, int64_t* n_kept, void* stream) {
+    if (!ctx || !res || !n_kept || cap < 0 || (cap > 0 && (!fits || !state))) return HT_ERR_INVALID_ARG;
+    if (radius < 0 || radius > 64) return fail(ctx, HT_ERR_INVALID_ARG, "merge radius must be in [0, 64]");
+    if (res->mem != HT_HOST && res->mem != HT_DEVICE) return fail(ctx, HT_ERR_INVALID_ARG, "res.mem must be HT_HOST or HT_DEVICE");
+    if (!ctx->have_results) return fail(ctx, HT_ERR_STATE, "ht_merge needs a preceding ht_process");
+    cudaStream_t s = nullptr;
+    if (int st0 = resolve_stream(ctx, stream, &s)) return st0;
+    CU(ctx->mkept.ensure(1, nullptr));
+    CU(cudaMemsetAsync(ctx->mkept.p, 0, sizeof(unsigned long long), s));
+    MergeParams p{};
+    p.x = ctx->cx;
+    p.y = ctx->cy;
+    p.peak_cap = res->peak_cap;
+    p.pair_cap = res->pair_cap;
+    p.kept = ctx->mkept.p;
+    p.n_phi = ctx->grid.n_phi;
+    p.n_d0 = ctx->grid.n_d0;
+    p.n_kappa = ctx->grid.n_kappa;
+    p.radius = radius;
+    if (res->mem == HT_DEVICE) {
+        p.peaks = res->peaks;
+        p.po = res->peak_offsets;
+        p.hidx = res->hit_idx;
+        p.n_peaks = res->counts;
+        p.cap = cap;
+        p.fits = fits;
+        p.state = state;
+        CU(launch_merge(p, s));
+        // the counter is unsigned 64-bit and n_kept int64: same bytes for any count
+        CU(cudaMemcpyAsync(n_kept, ctx->mkept.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        return HT_OK;
+    }
+    // host results: the context still holds them on the device
+    const int64_t n = std::min(std::min(res->counts[0], res->peak_cap), cap);
+    *n_kept = 0;
+    if (n <= 0) return HT_OK;
+    CU(ctx->fits.ensure(n, &ctx->gen));
+    CU(ctx->mstate.ensure(n, nullptr));
+    CU(cudaMemcpyAsync(ctx->fits.p, fits, n * sizeof(ht_track), cudaMemcpyHostToDevice, s));
+    p.peaks = ctx->peaks.p;
+    p.po = ctx->peakoff.p;
+    p.hidx = ctx->hitidx.p;
+    p.n_peaks = ctx->d_scal + 6;
+    p.cap = n;
+    p.fits = ctx->fits.p;
+    p.state = ctx->mstate.p;
+    CU(launch_merge(p, s));
+    CU(cudaMemcpyAsync(state, ctx->mstate.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->mkept.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *n_kept = ctx->h_pinned[2];
     return HT_OK;
 }
 

@@ -143,6 +143,21 @@ struct FitParams {
     int32_t nk;
 };
 cudaError_t launch_fit(const FitParams& p, cudaStream_t s);
+// duplicate and mirror merging of fitted candidates (ht_merge.cu)
+struct MergeParams {
+    const float* x;
+    const float* y;
+    const ht_peak* peaks;     // sorted by (event, linear index)
+    const int64_t* po;
+    const int32_t* hidx;
+    const int64_t* n_peaks;   // device scalar: the true peak count
+    int64_t peak_cap, pair_cap, cap;
+    const ht_track* fits;
+    int32_t* state;
+    unsigned long long* kept; // device counter, zeroed by the caller
+    int32_t n_phi, n_d0, n_kappa, radius;
+};
+cudaError_t launch_merge(const MergeParams& p, cudaStream_t s);
 // second Hough transform for displaced vertices (ht_vertex.cu)
 struct VertexParams {
     const ht_peak* peaks;

@@ -52,7 +52,7 @@ HT_MODE_PLAIN = 1
 EXPORTS = ("ht_create", "ht_destroy", "ht_set_option", "ht_get_option", "ht_vote", "ht_peaks",
            "ht_associate", "ht_process", "ht_get_accumulator", "ht_get_tables", "ht_sync",
            "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_peaks_noalloc", "ht_check_rcp", "ht_strerror", "ht_last_error",
-           "ht_fit", "ht_vertices")
+           "ht_fit", "ht_vertices", "ht_merge")
 
 PEAK_DTYPE = np.dtype([("event", np.int32), ("i_phi", np.int32), ("i_d0", np.int32),
                        ("i_kappa", np.int32), ("votes", np.uint32)])
@@ -121,6 +121,7 @@ def load() -> ctypes.CDLL:
         "ht_peaks_noalloc": [P, P, i32, u32, P, i64, P, P],
         "ht_fit": [P, P, P, i64, P],
         "ht_vertices": [P, P, P, u32, P, i64, P, P],
+        "ht_merge": [P, P, P, i32, P, i64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -169,6 +170,18 @@ def _stream_ptr(stream):
             pass
         return None
     return getattr(stream, "cuda_stream", stream)
+
+
+def _on_stream(stream):
+    """Context in which torch allocates (and zero-fills) outputs on `stream`,
+    so that the fill is ordered before the library's kernels on it."""
+    import contextlib
+    import torch
+    if isinstance(stream, torch.cuda.Stream):
+        return torch.cuda.stream(stream)
+    if stream is not None:
+        return torch.cuda.stream(torch.cuda.ExternalStream(int(stream)))
+    return contextlib.nullcontext()
 
 
 class Hits:
@@ -372,9 +385,39 @@ def ht_fit(ctx, results, cap=None, stream=None):
         _check(load().ht_fit(ctx, ctypes.byref(results.struct), out.ctypes.data, n, _stream_ptr(stream)), ctx)
         return out[:n]
     import torch
-    out = torch.zeros(max(cap, 1) * TRACK_DTYPE.itemsize, dtype=torch.uint8, device=results.counts.device)
+    with _on_stream(stream):
+        out = torch.zeros(max(cap, 1) * TRACK_DTYPE.itemsize, dtype=torch.uint8, device=results.counts.device)
     _check(load().ht_fit(ctx, ctypes.byref(results.struct), _ptr(out), cap, _stream_ptr(stream)), ctx)
     return out
+
+
+HT_MERGE_KEPT, HT_MERGE_DUPLICATE, HT_MERGE_BACKWARD, HT_MERGE_UNFITTED = 1, 0, -1, -2
+
+
+def ht_merge(ctx, results, fits, radius=2, cap=None, stream=None):
+    """Duplicate and mirror merging of fitted candidates (see ht.h).  Host
+    results: (int32 state array, number kept).  Device results, with `fits`
+    the device buffer ht_fit returned: (CUDA int32 state tensor, CUDA int64
+    kept-count tensor)."""
+    lib = load()
+    if isinstance(results.counts, np.ndarray):
+        n = int(min(results.counts[0], results.peak_cap, len(fits) if cap is None else int(cap)))
+        f = np.ascontiguousarray(fits[:n], dtype=TRACK_DTYPE)
+        state = np.zeros(max(n, 1), np.int32)
+        kept = ctypes.c_int64()
+        _check(lib.ht_merge(ctx, ctypes.byref(results.struct), f.ctypes.data, int(radius), state.ctypes.data, n,
+                            ctypes.byref(kept), _stream_ptr(stream)), ctx)
+        return state[:n], int(kept.value)
+    import torch
+    cap = results.peak_cap if cap is None else int(cap)
+    assert fits.numel() >= cap * TRACK_DTYPE.itemsize, "fits buffer smaller than cap"
+    dev = results.counts.device
+    with _on_stream(stream):
+        state = torch.zeros(max(cap, 1), dtype=torch.int32, device=dev)
+        kept = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check(lib.ht_merge(ctx, ctypes.byref(results.struct), _ptr(fits), int(radius), _ptr(state), cap, _ptr(kept),
+                        _stream_ptr(stream)), ctx)
+    return state, kept
 
 
 class HtVGrid(ctypes.Structure):
@@ -402,8 +445,9 @@ def ht_vertices(ctx, vg, results, threshold, cap=None, stream=None):
             return out[: n.value].copy(), int(n.value)
     import torch
     dev = results.counts.device
-    out = torch.zeros(max(cap, 1) * VERTEX_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    with _on_stream(stream):
+        out = torch.zeros(max(cap, 1) * VERTEX_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     _check(lib.ht_vertices(ctx, ctypes.byref(v), ctypes.byref(results.struct), int(threshold), _ptr(out), cap,
                            _ptr(cnt), _stream_ptr(stream)), ctx)
     return out, cnt
@@ -432,6 +476,7 @@ class Context:
         self.grid = grid
         self.shape = (int(grid.n_phi), int(grid.n_d0), int(grid.n_kappa))
         self.handle = ht_create(grid, layer_r)
+        self._hits = None
 
     def close(self):
         if self.handle:
@@ -451,6 +496,9 @@ class Context:
         return ht_get_option(self.handle, key)
 
     def vote(self, hits: Hits, stream=None):
+        # device hits are borrowed: the later associate/fit/merge/vertices
+        # calls read them, so the context keeps them alive until the next batch
+        self._hits = hits
         ht_vote(self.handle, hits, stream)
 
     def peaks(self, threshold, cap=None):
@@ -460,6 +508,7 @@ class Context:
         return ht_associate(self.handle, window, n_peaks, cap)
 
     def process(self, hits: Hits, threshold, window, results: Results, stream=None, allow_overflow=False):
+        self._hits = hits  # borrowed device hits stay alive for fit/merge/vertices
         return ht_process(self.handle, hits, threshold, window, results, stream, allow_overflow)
 
     def accumulator(self, event=0):
@@ -482,6 +531,9 @@ class Context:
 
     def fit(self, results, cap=None, stream=None):
         return ht_fit(self.handle, results, cap, stream)
+
+    def merge(self, results, fits, radius=2, cap=None, stream=None):
+        return ht_merge(self.handle, results, fits, radius, cap, stream)
 
     def vertices(self, vg, results, threshold, cap=None, stream=None):
         return ht_vertices(self.handle, vg, results, threshold, cap, stream)
