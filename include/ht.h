@@ -345,6 +345,21 @@ int ht_peaks_noalloc(const ht_grid *grid, const uint32_t *acc, int32_t n_events,
  * Synchronous; allocates 16 bytes of device memory. */
 int ht_check_rcp(uint32_t first_bits, uint32_t count, uint64_t *out);
 
+/* Diagnostic (no paper counterpart): throughput ceilings of the operations
+ * the vote is made of, measured on the current device with CUDA events over
+ * one launch of 8 blocks of 256 threads per SM after a warm-up launch.
+ *   HT_MB_FP32     independent FP32 multiplies and adds (lane operations/s);
+ *   HT_MB_SHARED_RED  red.shared.add.u32 at random addresses of a 16 KB
+ *                  tile (increments/s, bank conflicts included);
+ *   HT_MB_FDIV     IEEE float32 divisions (divisions/s).
+ * `iters` is the per-thread iteration count (>= 1; each does 8 operations of
+ * the kind, FP32 16).  *rate receives operations per second.  Synchronous on
+ * the legacy default stream; allocates a few KB of device memory. */
+#define HT_MB_FP32 0
+#define HT_MB_SHARED_RED 1
+#define HT_MB_FDIV 2
+int ht_microbench(int32_t kind, int64_t iters, double *rate);
+
 const char *ht_strerror(int status);
 const char *ht_last_error(ht_ctx *ctx);
 

@@ -1551,4 +1551,21 @@ int ht_check_rcp(uint32_t first_bits, uint32_t count, uint64_t* out) {
     return HT_OK;
 }
 
+int ht_microbench(int32_t kind, int64_t iters, double* rate) {
+    ht_ctx* ctx = nullptr;
+    if (!rate || kind < HT_MB_FP32 || kind > HT_MB_FDIV || iters < 1) return HT_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float* sink = nullptr;
+    CU(cudaMalloc(&sink, sizeof(float) * (size_t)sms * 8));
+    float ms = 0.f;
+    double ops = 0.0;
+    const cudaError_t e = run_microbench(kind, iters, sms, sink, &ms, &ops);
+    cudaFree(sink);
+    CU(e);
+    *rate = ms > 0.f ? ops / (ms * 1e-3) : 0.0;
+    return HT_OK;
+}
+
 }  // extern "C"

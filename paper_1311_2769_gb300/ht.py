@@ -52,7 +52,7 @@ HT_MODE_PLAIN = 1
 EXPORTS = ("ht_create", "ht_destroy", "ht_set_option", "ht_get_option", "ht_vote", "ht_peaks",
            "ht_associate", "ht_process", "ht_get_accumulator", "ht_get_tables", "ht_sync",
            "ht_autotune", "ht_filter_stats", "ht_phase_times", "ht_peaks_noalloc", "ht_check_rcp", "ht_strerror", "ht_last_error",
-           "ht_fit", "ht_vertices", "ht_merge")
+           "ht_fit", "ht_vertices", "ht_merge", "ht_microbench")
 
 PEAK_DTYPE = np.dtype([("event", np.int32), ("i_phi", np.int32), ("i_d0", np.int32),
                        ("i_kappa", np.int32), ("votes", np.uint32)])
@@ -122,6 +122,7 @@ def load() -> ctypes.CDLL:
         "ht_fit": [P, P, P, i64, P],
         "ht_vertices": [P, P, P, u32, P, i64, P, P],
         "ht_merge": [P, P, P, i32, P, i64, P, P],
+        "ht_microbench": [i32, i64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -461,6 +462,16 @@ def vertices_host(t, n):
 def tracks_host(t, n):
     """The first n fits of a device fit buffer as a TRACK_DTYPE array."""
     return np.frombuffer(t.cpu().numpy().tobytes(), TRACK_DTYPE)[: int(n)].copy()
+
+
+HT_MB_FP32, HT_MB_SHARED_RED, HT_MB_FDIV = 0, 1, 2
+
+
+def ht_microbench(kind, iters):
+    """Measured throughput (operations/s) of one operation kind (see ht.h)."""
+    rate = ctypes.c_double()
+    _check(load().ht_microbench(int(kind), int(iters), ctypes.byref(rate)))
+    return rate.value
 
 
 def ht_check_rcp(first_bits, count):
