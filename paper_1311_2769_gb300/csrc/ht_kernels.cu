@@ -559,14 +559,19 @@ __global__ void order_kernel(const int32_t* offs, int32_t event0, int32_t n_even
 // A CTA stages rows i0-1 .. i0+R (phi wraps) x columns j0-1 .. j0+TD of one
 // event in shared memory, cells outside the d0 range marked absent, and tests
 // every interior cell at or above the threshold against its 26 neighbours
-// with the linear-order tie rule, leaving at the first failure.
+// with the linear-order tie rule.
 constexpr uint32_t kAbsent = 0xFFFFFFFFu;
+
+// shared column stride of the detection tile: kappa bins plus a pad that
+// keeps 16-byte rows for vector staging and shifts neighbour columns' banks
+__host__ __device__ __forceinline__ int detect_stride(int nk) { return (nk & 3) == 0 ? nk + 4 : nk + 1; }
 
 __global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const int R, const int TD) {
     extern __shared__ __align__(16) uint32_t tile[];
     const int nk = p.nk, nkw = p.nkw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int tcols = TD + 2;
+    const int cs = detect_stride(nk);  // padded column stride: neighbour columns fall in different banks
     const int tiles_i = (p.nphi + R - 1) / R, tiles_j = (p.nd + TD - 1) / TD;
     const int64_t items = (int64_t)p.n_events * tiles_i * tiles_j;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
@@ -577,14 +582,17 @@ __global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const i
         const int nr = min(R, p.nphi - i0), nj = min(TD, p.nd - j0);
         const uint32_t* A = p.acc + (int64_t)e * p.cells;
         __syncthreads();
-        // stage (nr + 2) x (nj + 2) columns
-        const int ncolumns = (nr + 2) * (nj + 2);
-        for (int cc = warp; cc < ncolumns; cc += nw) {
-            const int ri = cc / (nj + 2), cj = cc - (cc / (nj + 2)) * (nj + 2);
+        // stage (nr + 2) x (nj + 2) columns, warp by warp in row-major order
+        int ri = 0, cj = warp;
+        while (cj >= nj + 2) {
+            cj -= nj + 2;
+            ++ri;
+        }
+        for (; ri < nr + 2;) {
             int ii = i0 - 1 + ri;
-            ii = ((ii % p.nphi) + p.nphi) % p.nphi;
+            ii = ii < 0 ? ii + p.nphi : (ii >= p.nphi ? ii - p.nphi : ii);
             const int jj = j0 - 1 + cj;
-            uint32_t* dst = tile + ((int64_t)ri * tcols + cj) * nk;
+            uint32_t* dst = tile + (ri * tcols + cj) * cs;
             if (jj < 0 || jj >= p.nd) {
                 for (int kk = lane; kk < nk; kk += 32) dst[kk] = kAbsent;
             } else {
@@ -597,14 +605,28 @@ __global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const i
                     for (int kk = lane; kk < nk; kk += 32) dst[kk] = src[kk];
                 }
             }
+            cj += nw;
+            while (cj >= nj + 2) {
+                cj -= nj + 2;
+                ++ri;
+            }
         }
         __syncthreads();
         // interior columns: warp per (row, column), lanes over kappa.  Every lane
         // reads its 3x3x3 box (absent neighbours read as -1 in int32, so they
         // never reject) and compares against the maximum of the neighbours that
         // precede it in linear order (strictly) and of those that follow it.
-        for (int cc = warp; cc < nr * nj; cc += nw) {
-            const int r = cc / nj, j = cc - (cc / nj) * nj;
+        int r = 0, j = warp;
+        while (j >= nj) {
+            j -= nj;
+            ++r;
+        }
+        for (; r < nr; j += nw) {
+            while (j >= nj) {
+                j -= nj;
+                ++r;
+            }
+            if (r >= nr) break;
             const int i = i0 + r;
             const int64_t col = ((int64_t)e * p.nphi + i) * p.nd + (j0 + j);
             // row di = -1 / +1 precedes row i unless the phi wrap makes it follow
@@ -616,15 +638,15 @@ __global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const i
                 const int kk = k0 + lane;
                 bool pk = false;
                 if (kk < nk) {
-                    const int v = (int)tile[((int64_t)(r + 1) * tcols + (j + 1)) * nk + kk];
+                    const int v = (int)tile[((r + 1) * tcols + (j + 1)) * cs + kk];
                     int mE = -1, mL = -1;
 #pragma unroll
                     for (int di = -1; di <= 1; ++di) {
                         if (single && di != 0) continue;
-                        const int* rowp = reinterpret_cast<const int*>(tile) + ((int64_t)(r + 1 + di) * tcols) * nk;
+                        const int* rowp = reinterpret_cast<const int*>(tile) + ((r + 1 + di) * tcols) * cs;
 #pragma unroll
                         for (int dj = -1; dj <= 1; ++dj) {
-                            const int* cp2 = rowp + (j + 1 + dj) * nk;
+                            const int* cp2 = rowp + (j + 1 + dj) * cs;
                             const int u0 = cp2[kk];
                             const int um = kk > 0 ? cp2[kk - 1] : -1;
                             const int up = kk + 1 < nk ? cp2[kk + 1] : -1;
@@ -1606,9 +1628,10 @@ static int warp_grid(int64_t ncols, int threads) {
 // detect tile: R interior rows x TD interior columns, halo included, ~96 KB
 void detect_tile(int nphi, int nd, int nk, int* R, int* TD) {
     const int64_t budget = 96 * 1024 / 4;  // words
+    const int64_t cs = detect_stride(nk);
     int td = nd;
-    while (td > 1 && (int64_t)3 * (td + 2) * nk > budget) td = (td + 1) / 2;
-    int r = (int)(budget / ((int64_t)(td + 2) * nk)) - 2;
+    while (td > 1 && (int64_t)3 * (td + 2) * cs > budget) td = (td + 1) / 2;
+    int r = (int)(budget / ((int64_t)(td + 2) * cs)) - 2;
     r = std::max(1, std::min(r, nphi));
     *R = r;
     *TD = td;
@@ -1617,7 +1640,7 @@ void detect_tile(int nphi, int nd, int nk, int* R, int* TD) {
 size_t detect_smem(int nphi, int nd, int nk) {
     int R, TD;
     detect_tile(nphi, nd, nk, &R, &TD);
-    return (size_t)(R + 2) * (TD + 2) * nk * 4;
+    return (size_t)(R + 2) * (TD + 2) * detect_stride(nk) * 4;
 }
 
 cudaError_t detect_prepare(int nphi, int nd, int nk) {
