@@ -141,6 +141,10 @@ typedef struct {
                                       as many as fit 9 KB of shared memory per warp, 256..1024);
                                       a column block with more peaks is walked once per block of
                                       cursors.  Reading gives the resolved value. */
+#define HT_OPT_HOST_CHUNKS 15      /* ht_process with host results (batched mode): run the batch in at
+                                      least this many waves and copy each wave's peaks and CSR to the
+                                      host while later waves compute (1..64, default 16; 1 = copy after
+                                      the whole batch) */
 
 /* Vote modes.  HT_VOTE_POINT: a hit votes, in each (phi0, d0) column, for the
  * kappa bin of its curve at the column's centre (Section 3's vote, point

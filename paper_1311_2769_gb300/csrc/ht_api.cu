@@ -86,6 +86,7 @@ struct ht_ctx {
     int prune = 3;                   // bit 0: vote, bit 1: association drop hits without a d0 band
     int vote_mode = HT_VOTE_POINT;
     int acap = 0;  // association row cursors per warp (0 = auto)
+    int host_chunks = 16;  // host results: minimum waves, each copied out while the next computes
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
@@ -142,6 +143,13 @@ struct ht_ctx {
 
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;  // used when the caller passes the legacy NULL stream
+    // host results copied wave by wave: per-wave running totals {peaks, pairs}
+    // (pinned, written by the step), an event after each wave, a copy stream
+    bool wave_marks = false;
+    std::vector<cudaEvent_t> wave_ev;
+    int64_t* h_wave = nullptr;
+    int h_wave_n = 0;
+    cudaStream_t copy_stream = nullptr;
     bool pending_check = false;
     const ht_results* pending_res = nullptr;
     ht_results pending_copy{};
@@ -701,6 +709,11 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
                              window, single, s);
         if (st) return st;
         if (single && (st = mark(ctx, 2, s))) return st;
+        if (ctx->wave_marks) {  // running totals after this wave, then its event (host copies follow it)
+            const int wi = e0 / step;
+            CU(cudaMemcpyAsync(ctx->h_wave + 2 * wi, ctx->d_scal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CU(cudaEventRecord(ctx->wave_ev[wi], s));
+        }
         ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode != HT_VOTE_POINT ? 1 : 0);
     }
     if (single && (st = mark(ctx, 3, s))) return st;
@@ -836,6 +849,9 @@ int ht_destroy(ht_ctx* ctx) {
         if (p) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t ev : ctx->wave_ev) cudaEventDestroy(ev);
+    if (ctx->h_wave) cudaFreeHost(ctx->h_wave);
     ctx->sx.release();
     ctx->sy.release();
     ctx->slayer.release();
@@ -908,6 +924,10 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
                 return fail(ctx, HT_ERR_INVALID_ARG, "association cursors must be 0 or a multiple of 32 up to 65536");
             ctx->acap = (int)value;
             break;
+        case HT_OPT_HOST_CHUNKS:
+            if (value < 1 || value > 64) return fail(ctx, HT_ERR_INVALID_ARG, "host chunks must be in [1, 64]");
+            ctx->host_chunks = (int)value;
+            break;
         case HT_OPT_VOTE_MODE: {
             if (value != HT_VOTE_POINT && value != HT_VOTE_RANGE && value != HT_VOTE_LINE)
                 return fail(ctx, HT_ERR_INVALID_ARG, "vote mode must be HT_VOTE_POINT, HT_VOTE_RANGE or HT_VOTE_LINE");
@@ -962,6 +982,7 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_ATILE_D0: *value = ctx->a_tile_d; break;
         case HT_OPT_VOTE_MODE: *value = ctx->vote_mode; break;
         case HT_OPT_ASSOC_CURSORS: *value = ctx->a_cap; break;
+        case HT_OPT_HOST_CHUNKS: *value = ctx->host_chunks; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
@@ -1114,7 +1135,32 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         poff = ctx->peakoff.p;
         hidx = ctx->hitidx.p;
     }
-    const bool graph = ctx->use_graph && ctx->mode == HT_MODE_BATCHED;
+    // host results in batched mode: at least host_chunks waves, each copied
+    // to the host on the copy stream while the following waves compute
+    const bool pipe = res->mem == HT_HOST && ctx->mode == HT_MODE_BATCHED && ctx->host_chunks > 1 &&
+                      ctx->c_events > 1;
+    int32_t step = epw;
+    if (pipe) step = std::min<int32_t>(epw, (ctx->c_events + ctx->host_chunks - 1) / ctx->host_chunks);
+    const int32_t nwaves = ctx->c_events > 0 ? (ctx->c_events + step - 1) / step : 0;
+    ctx->wave_marks = pipe;
+    if (pipe) {
+        while ((int32_t)ctx->wave_ev.size() < nwaves) {
+            cudaEvent_t ev = nullptr;
+            CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            ctx->wave_ev.push_back(ev);
+        }
+        if (ctx->h_wave_n < nwaves) {
+            if (ctx->h_wave) cudaFreeHost(ctx->h_wave);
+            ctx->h_wave = nullptr;
+            ctx->h_wave_n = 0;
+            CU(cudaMallocHost(&ctx->h_wave, 2 * sizeof(int64_t) * (size_t)nwaves));
+            ctx->h_wave_n = nwaves;
+        }
+        if (!ctx->copy_stream) CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    }
+    // the wave-by-wave copies wait on events recorded by direct launches (a
+    // few dozen launches per batch), so that path does not replay the graph
+    const bool graph = ctx->use_graph && ctx->mode == HT_MODE_BATCHED && !pipe;
     if (graph) {
         GraphKey key{};
         key.ptrs[0] = ctx->cx;
@@ -1130,7 +1176,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         key.vals[3] = window;
         key.vals[4] = pcap;
         key.vals[5] = qcap;
-        key.vals[6] = epw;
+        key.vals[6] = step;
         key.vals[7] = ctx->gen;
         key.vals[8] = ctx->r_tile_phi * 100000 + ctx->r_tile_d;
         key.vals[9] = ctx->r_threads;
@@ -1145,7 +1191,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
             ctx->gvalid = false;
             cudaGraph_t g = nullptr;
             CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, epw, s);
+            st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, step, s);
             cudaError_t ce = cudaStreamEndCapture(s, &g);
             if (st) {
                 if (g) cudaGraphDestroy(g);
@@ -1160,7 +1206,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         }
         CU(cudaGraphLaunch(ctx->gexec, s));
     } else {
-        st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, epw, s);
+        st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, step, s);
         if (st) return st;
     }
     ctx->have_results = true;
@@ -1172,17 +1218,47 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         return HT_OK;
     }
     CU(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scal + 6, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    // stored peaks / pairs already on the host (wave by wave)
+    int64_t p_done = 0, q_done = 0;
+    if (pipe) {
+        cudaStream_t cs = ctx->copy_stream;
+        for (int32_t w = 0; w < nwaves; ++w) {
+            CU(cudaEventSynchronize(ctx->wave_ev[w]));
+            const int64_t p_cur = std::min(ctx->h_wave[2 * w], pcap), q_cur = std::min(ctx->h_wave[2 * w + 1], qcap);
+            CU(cudaStreamWaitEvent(cs, ctx->wave_ev[w], 0));
+            if (p_cur > p_done) {
+                CU(cudaMemcpyAsync(res->peaks + p_done, peaks + p_done, (p_cur - p_done) * sizeof(ht_peak),
+                                   cudaMemcpyDeviceToHost, cs));
+                CU(cudaMemcpyAsync(res->peak_offsets + p_done, poff + p_done, (p_cur - p_done) * sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, cs));
+                p_done = p_cur;
+            }
+            if (q_cur > q_done) {
+                CU(cudaMemcpyAsync(res->hit_idx + q_done, hidx + q_done, (q_cur - q_done) * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, cs));
+                q_done = q_cur;
+            }
+        }
+    }
     CU(cudaStreamSynchronize(s));
     st = read_err(ctx);
-    if (st) return st;
+    if (st) {
+        if (pipe) cudaStreamSynchronize(ctx->copy_stream);
+        return st;
+    }
     const int64_t np = ctx->h_pinned[0], nq = ctx->h_pinned[1];
     res->counts[0] = np;
     res->counts[1] = nq;
     const int64_t cp = std::min(np, pcap), cq = std::min(nq, qcap);
-    if (cp > 0) CU(cudaMemcpyAsync(res->peaks, peaks, cp * sizeof(ht_peak), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(res->peak_offsets, poff, (cp + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (cq > 0) CU(cudaMemcpyAsync(res->hit_idx, hidx, cq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    // the rest (everything, without the wave copies) and the final row end
+    if (cp > p_done) CU(cudaMemcpyAsync(res->peaks + p_done, peaks + p_done, (cp - p_done) * sizeof(ht_peak),
+                                        cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(res->peak_offsets + std::min(p_done, cp), poff + std::min(p_done, cp),
+                       (cp + 1 - std::min(p_done, cp)) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (cq > q_done) CU(cudaMemcpyAsync(res->hit_idx + q_done, hidx + q_done, (cq - q_done) * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (pipe) CU(cudaStreamSynchronize(ctx->copy_stream));
     if (np > pcap || nq > qcap)
         return fail(ctx, HT_ERR_OVERFLOW, "%lld peaks (cap %lld), %lld pairs (cap %lld)", (long long)np,
                     (long long)pcap, (long long)nq, (long long)qcap);
@@ -1495,6 +1571,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
             float abest = 1e30f;
             int ap_best = 0, ad_best = 0;
             const int32_t epw = events_per_wave(ctx, ctx->c_events);
+            ctx->wave_marks = false;  // no host copies here
             for (int ap : {1, 2, 4, 8}) {
                 if (ap > ctx->grid.n_phi) continue;
                 for (int ad : {nd, 32, 16, 8}) {
