@@ -443,8 +443,16 @@ def run_gpu(args):
         fit_ms.append(f0.elapsed_time(f1))
     n_fit = int(min(counts[0], res.peak_cap))
     fitted = int((fits.view(torch.int32)[0::12][:n_fit] == 1).sum().item())  # status, every 48 bytes
+    # binary64 work of the fit: 23 operations per row hit (14 for the sums,
+    # 9 for the residual, its square root counted as one) + ~45 per candidate
+    fp64_rate = ht.ht_microbench(ht.HT_MB_FP64, 2500)
+    fit_ops = 23.0 * float(min(counts[1], res.pair_cap)) + 45.0 * n_fit
     fit_info = {"ms": float(np.median(fit_ms)), "candidates": n_fit, "fitted": fitted,
-                "candidates_per_s": n_fit / (float(np.median(fit_ms)) / 1e3)}
+                "candidates_per_s": n_fit / (float(np.median(fit_ms)) / 1e3),
+                "roofline": {"bound": "fp64", "achieved": fit_ops / (float(np.median(fit_ms)) / 1e3) / 1e12,
+                             "peak": fp64_rate / 1e12, "unit": "T binary64 ops/s",
+                             "frac": fit_ops / (float(np.median(fit_ms)) / 1e3) / fp64_rate,
+                             "peak_basis": "measured binary64 multiply/add rate (ht_microbench)"}}
     # duplicate and mirror merging of those fits (radius 2; not in the step)
     merge_ms = []
     for _ in range(3):

@@ -355,13 +355,15 @@ int ht_check_rcp(uint32_t first_bits, uint32_t count, uint64_t *out);
  *   HT_MB_FP32     independent FP32 multiplies and adds (lane operations/s);
  *   HT_MB_SHARED_RED  red.shared.add.u32 at random addresses of a 16 KB
  *                  tile (increments/s, bank conflicts included);
- *   HT_MB_FDIV     IEEE float32 divisions (divisions/s).
+ *   HT_MB_FDIV     IEEE float32 divisions (divisions/s);
+ *   HT_MB_FP64     independent binary64 multiplies and adds (operations/s).
  * `iters` is the per-thread iteration count (>= 1; each does 8 operations of
- * the kind, FP32 16).  *rate receives operations per second.  Synchronous on
+ * the kind, FP32 and FP64 16).  *rate receives operations per second.  Synchronous on
  * the legacy default stream; allocates a few KB of device memory. */
 #define HT_MB_FP32 0
 #define HT_MB_SHARED_RED 1
 #define HT_MB_FDIV 2
+#define HT_MB_FP64 3
 int ht_microbench(int32_t kind, int64_t iters, double *rate);
 
 const char *ht_strerror(int status);

@@ -1630,7 +1630,7 @@ int ht_check_rcp(uint32_t first_bits, uint32_t count, uint64_t* out) {
 
 int ht_microbench(int32_t kind, int64_t iters, double* rate) {
     ht_ctx* ctx = nullptr;
-    if (!rate || kind < HT_MB_FP32 || kind > HT_MB_FDIV || iters < 1) return HT_ERR_INVALID_ARG;
+    if (!rate || kind < HT_MB_FP32 || kind > HT_MB_FP64 || iters < 1) return HT_ERR_INVALID_ARG;
     int dev = 0, sms = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -179,7 +179,8 @@ struct VertexParams {
 cudaError_t launch_vertex_vote(const VertexParams& p, cudaStream_t s);
 cudaError_t launch_vertex_rows(const VertexParams& p, bool emit, cudaStream_t s);
 cudaError_t launch_rcp_check(uint32_t first_bits, uint32_t count, unsigned long long* out, cudaStream_t s);
-// throughput microbenchmarks (ht_microbench.cu): kind 0 FP32 mul/add, 1 shared reductions, 2 FP32 IEEE division
+// throughput microbenchmarks (ht_microbench.cu): kind 0 FP32 mul/add, 1 shared reductions, 2 FP32 IEEE
+// division, 3 binary64 mul/add
 cudaError_t run_microbench(int kind, int64_t iters, int sms, float* sink, float* ms, double* ops);
 
 }  // namespace ht

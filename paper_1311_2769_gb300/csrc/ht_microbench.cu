@@ -1,8 +1,9 @@
 // ht_microbench.cu — throughput ceilings of the operations the vote is made
 // of, measured on the GPU the library runs on: FP32 multiply/add lane
 // operations, predicated shared-memory reductions (the vote's increment) at
-// random addresses of an accumulator tile, and IEEE float32 divisions.  The
-// vote's fractions of these ceilings say which one binds it.
+// random addresses of an accumulator tile, IEEE float32 divisions, and
+// binary64 multiply/add (the circle fit's and the merge's arithmetic).  The
+// kernels' fractions of these ceilings say which one binds them.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,6 +31,22 @@ __global__ void mb_fp32_kernel(int64_t iters, float seed, float* sink) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) s += a[c];
     if (s == 12345.678f) sink[blockIdx.x] = s;  // keeps the chains live
+}
+
+// 8 independent chains of one binary64 multiply and one add each.
+__global__ void mb_fp64_kernel(int64_t iters, float seed, float* sink) {
+    double a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = (double)seed + (double)(threadIdx.x + c);
+    const double m = 0.999, k = 1e-3;
+    for (int64_t t = 0; t < iters; ++t) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = __dadd_rn(__dmul_rn(a[c], m), k);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == 12345.678) sink[blockIdx.x] = (float)s;
 }
 
 // 8 independent chains of IEEE divisions x -> k / x (stays finite).
@@ -87,7 +104,8 @@ cudaError_t run_microbench(int kind, int64_t iters, int sms, float* sink, float*
     auto launch = [&](int64_t n) {
         if (kind == 0) mb_fp32_kernel<<<blocks, kMbThreads>>>(n, 1.0f, sink);
         else if (kind == 1) mb_red_kernel<<<blocks, kMbThreads>>>(n, 1.0f, sink);
-        else mb_fdiv_kernel<<<blocks, kMbThreads>>>(n, 1.0f, sink);
+        else if (kind == 2) mb_fdiv_kernel<<<blocks, kMbThreads>>>(n, 1.0f, sink);
+        else mb_fp64_kernel<<<blocks, kMbThreads>>>(n, 1.0f, sink);
     };
     launch(iters / 8 + 1);  // warm-up
     cudaEventRecord(e0);
@@ -96,7 +114,7 @@ cudaError_t run_microbench(int kind, int64_t iters, int sms, float* sink, float*
     e = cudaGetLastError();
     if (!e) e = cudaEventSynchronize(e1);
     if (!e) e = cudaEventElapsedTime(ms, e0, e1);
-    const double per_iter = kind == 0 ? 16.0 : 8.0;  // fp32: 8 chains x (mul + add)
+    const double per_iter = (kind == 0 || kind == 3) ? 16.0 : 8.0;  // 8 chains x (mul + add)
     *ops = (double)blocks * kMbThreads * (double)iters * per_iter;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

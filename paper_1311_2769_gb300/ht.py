@@ -465,7 +465,7 @@ def tracks_host(t, n):
     return np.frombuffer(t.cpu().numpy().tobytes(), TRACK_DTYPE)[: int(n)].copy()
 
 
-HT_MB_FP32, HT_MB_SHARED_RED, HT_MB_FDIV = 0, 1, 2
+HT_MB_FP32, HT_MB_SHARED_RED, HT_MB_FDIV, HT_MB_FP64 = 0, 1, 2, 3
 
 
 def ht_microbench(kind, iters):

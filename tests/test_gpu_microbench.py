@@ -26,8 +26,9 @@ def test_microbench_rates(ht):
     assert 0.1 * lanes * 0.5e9 < fp32 < lanes * 2.5e9, fp32
     red = ht.ht_microbench(ht.HT_MB_SHARED_RED, 5000)
     div = ht.ht_microbench(ht.HT_MB_FDIV, 5000)
-    assert 0 < red < fp32 and 0 < div < fp32, (red, div, fp32)
-    for kind, iters in ((3, 10), (-1, 10), (ht.HT_MB_FP32, 0)):
+    fp64 = ht.ht_microbench(ht.HT_MB_FP64, 2000)
+    assert 0 < red < fp32 and 0 < div < fp32 and 0 < fp64 < fp32, (red, div, fp64, fp32)
+    for kind, iters in ((4, 10), (-1, 10), (ht.HT_MB_FP32, 0)):
         with pytest.raises(ht.HtError) as ei:
             ht.ht_microbench(kind, iters)
         assert ei.value.status == ht.HT_ERR_INVALID_ARG
