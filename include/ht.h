@@ -145,6 +145,11 @@ typedef struct {
                                       least this many waves and copy each wave's peaks and CSR to the
                                       host while later waves compute (1..64, default 16; 1 = copy after
                                       the whole batch) */
+#define HT_OPT_ASSOC_INDEX 16      /* 1: ht_process associates point votes through a per-(event,
+                                      layer) index of hit angles, binning only the hits whose exact
+                                      curvature can fall in a peak's window (needs layer ids and at
+                                      most 32 layers); 0 (default): every hit in every column.  Same
+                                      rows either way. */
 
 /* Vote modes.  HT_VOTE_POINT: a hit votes, in each (phi0, d0) column, for the
  * kappa bin of its curve at the column's centre (Section 3's vote, point

@@ -87,6 +87,14 @@ struct ht_ctx {
     int vote_mode = HT_VOTE_POINT;
     int acap = 0;  // association row cursors per warp (0 = auto)
     int host_chunks = 16;  // host results: minimum waves, each copied out while the next computes
+    int assoc_index = 0;   // 1: point association through the per-layer angular index when hits carry layers
+    bool use_index = false;           // the staged batch uses it (set before each step)
+    const int8_t* clayer = nullptr;   // layer ids of the staged batch (device)
+    const ht_peak* cur_peaks = nullptr;  // the step's peak array (device)
+    DBuf<int32_t> ibcount, ibcursor, ihid, itab;
+    DBuf<int64_t> ibstart;
+    DBuf<uint32_t> ir2min, ir2max;
+    DBuf<float> itheta;
     int64_t budget = kDefaultBudget;
     bool count_stages = false;
     bool use_graph = true;
@@ -451,15 +459,57 @@ int stage_hits(ht_ctx* ctx, const ht_hits* h, cudaStream_t s) {
         ctx->cx = ctx->sx.p;
         ctx->cy = ctx->sy.p;
         ctx->coffs = ctx->soffs.p;
+        ctx->clayer = lay;
         if (n) CU(launch_validate(ctx->cx, ctx->cy, lay, n, ctx->coffs, ne, ctx->n_layers, ctx->d_err, s));
     } else {
         ctx->cx = h->x;
         ctx->cy = h->y;
         ctx->coffs = h->event_offsets;
+        ctx->clayer = h->layer;
         CU(launch_validate(h->x, h->y, h->layer, n, h->event_offsets, ne, ctx->n_layers, ctx->d_err, s));
     }
     ctx->c_hits = n;
     ctx->c_events = ne;
+    return HT_OK;
+}
+
+// Decide whether the staged batch associates through the angular index
+// (point voting, layer ids present, at most 32 layers) and size its buffers;
+// called before any capture.
+int ensure_index(ht_ctx* ctx) {
+    ctx->use_index = ctx->assoc_index && ctx->vote_mode == HT_VOTE_POINT && ctx->clayer && ctx->n_layers >= 1 &&
+                     ctx->n_layers <= 32 && ctx->c_hits > 0 && ctx->c_events > 0;
+    if (!ctx->use_index) return HT_OK;
+    const int64_t nb = (int64_t)ctx->c_events * ctx->n_layers;
+    CU(ctx->ibcount.ensure(nb, &ctx->gen));
+    CU(ctx->ibcursor.ensure(nb, &ctx->gen));
+    CU(ctx->ibstart.ensure(nb + 1, &ctx->gen));
+    CU(ctx->ir2min.ensure(nb, &ctx->gen));
+    CU(ctx->ir2max.ensure(nb, &ctx->gen));
+    CU(ctx->itheta.ensure(ctx->c_hits, &ctx->gen));
+    CU(ctx->ihid.ensure(ctx->c_hits, &ctx->gen));
+    CU(ctx->itab.ensure(nb * 257, &ctx->gen));
+    return HT_OK;
+}
+
+int build_index(ht_ctx* ctx, cudaStream_t s) {
+    IndexParams ip{};
+    ip.x = ctx->cx;
+    ip.y = ctx->cy;
+    ip.layer = ctx->clayer;
+    ip.offs = ctx->coffs;
+    ip.n_events = ctx->c_events;
+    ip.nl = ctx->n_layers;
+    ip.bcount = ctx->ibcount.p;
+    ip.bstart = ctx->ibstart.p;
+    ip.bcursor = ctx->ibcursor.p;
+    ip.r2min = ctx->ir2min.p;
+    ip.r2max = ctx->ir2max.p;
+    ip.theta = ctx->itheta.p;
+    ip.hid = ctx->ihid.p;
+    ip.tab = ctx->itab.p;
+    ip.scratch = ctx->scratch.p;
+    CU(launch_index_build(ip, s));
     return HT_OK;
 }
 
@@ -655,6 +705,34 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* orde
         const int st = mark(ctx, 4, s);
         if (st) return st;
     }
+    if (!range && ctx->use_index) {
+        AssocIndexParams q{};
+        q.a = a;
+        q.a.x = ctx->cx;
+        q.a.y = ctx->cy;
+        q.a.offs = ctx->coffs;
+        q.a.n_hits = ctx->c_hits;
+        q.a.cphi = ctx->d_cphi;
+        q.a.sphi = ctx->d_sphi;
+        q.a.dtab = ctx->d_dtab;
+        q.a.K = ctx->K;
+        q.a.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+        q.peaks = ctx->cur_peaks;
+        q.lo_dev = ctx->d_scal + 2;
+        q.hi_dev = ctx->d_scal + 0;
+        q.theta = ctx->itheta.p;
+        q.hid = ctx->ihid.p;
+        q.tab = ctx->itab.p;
+        q.bstart = ctx->ibstart.p;
+        q.r2min = ctx->ir2min.p;
+        q.r2max = ctx->ir2max.p;
+        q.nl = ctx->n_layers;
+        q.kmin = ctx->grid.kappa_min;
+        q.dk = (float)(((double)ctx->grid.kappa_max - (double)ctx->grid.kappa_min) / (double)ctx->grid.n_kappa);
+        q.err = ctx->d_err;
+        CU(launch_assoc_index(q, s));
+        return HT_OK;
+    }
     return launch_assoc_ctx(ctx, a, event0, ne, order, range ? 2 : 0, s);
 }
 
@@ -693,6 +771,11 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
     // kernels per wave: [order] vote, detect, scan x3, emit, scan x3, assoc
     ctx->launches = 1;  // finalize
     int st = HT_OK;
+    ctx->cur_peaks = peaks;
+    if (ctx->use_index) {  // count, scan x3, scatter, sort
+        if ((st = build_index(ctx, s))) return st;
+        ctx->launches += 6;
+    }
     const bool single = ctx->c_events <= step;  // phase timing needs one wave
     for (int32_t e0 = 0; e0 < ctx->c_events; e0 += step) {
         const int32_t ne = std::min(step, ctx->c_events - e0);
@@ -726,6 +809,11 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
 int read_err(ht_ctx* ctx) {
     int32_t err = 0;
     CU(cudaMemcpy(&err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (err & 8) {
+        CU(cudaMemset(ctx->d_err, 0, sizeof(int32_t)));
+        return fail(ctx, HT_ERR_CUDA, "internal: an association row through the angular index came out with "
+                                      "another length than its window sum");
+    }
     if (err) {
         CU(cudaMemset(ctx->d_err, 0, sizeof(int32_t)));
         return fail(ctx, HT_ERR_INVALID_ARG, "invalid hits in batch:%s%s%s", (err & 1) ? " non-finite or |coordinate|>1e4" : "",
@@ -868,6 +956,14 @@ int ht_destroy(ht_ctx* ctx) {
     ctx->hitidx.release();
     ctx->fits.release();
     ctx->mstate.release();
+    ctx->ibcount.release();
+    ctx->ibcursor.release();
+    ctx->ihid.release();
+    ctx->itab.release();
+    ctx->ibstart.release();
+    ctx->ir2min.release();
+    ctx->ir2max.release();
+    ctx->itheta.release();
     ctx->mkept.release();
     ctx->vacc.release();
     ctx->vrow.release();
@@ -928,6 +1024,11 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             if (value < 1 || value > 64) return fail(ctx, HT_ERR_INVALID_ARG, "host chunks must be in [1, 64]");
             ctx->host_chunks = (int)value;
             break;
+        case HT_OPT_ASSOC_INDEX:
+            if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "assoc index must be 0 or 1");
+            ctx->assoc_index = (int)value;
+            ctx->gvalid = false;
+            break;
         case HT_OPT_VOTE_MODE: {
             if (value != HT_VOTE_POINT && value != HT_VOTE_RANGE && value != HT_VOTE_LINE)
                 return fail(ctx, HT_ERR_INVALID_ARG, "vote mode must be HT_VOTE_POINT, HT_VOTE_RANGE or HT_VOTE_LINE");
@@ -983,6 +1084,7 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_VOTE_MODE: *value = ctx->vote_mode; break;
         case HT_OPT_ASSOC_CURSORS: *value = ctx->a_cap; break;
         case HT_OPT_HOST_CHUNKS: *value = ctx->host_chunks; break;
+        case HT_OPT_ASSOC_INDEX: *value = ctx->assoc_index; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
@@ -1124,6 +1226,8 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
     if (st) return st;
     const int64_t pcap = res->peak_cap, qcap = res->pair_cap;
     CU(ctx->paircnt.ensure(std::max<int64_t>(pcap, 1), &ctx->gen));
+    st = ensure_index(ctx);
+    if (st) return st;
     ht_peak* peaks = res->peaks;
     int64_t* poff = res->peak_offsets;
     int32_t* hidx = res->hit_idx;
@@ -1170,6 +1274,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         key.ptrs[4] = poff;
         key.ptrs[5] = hidx;
         key.ptrs[6] = s;
+        key.ptrs[7] = ctx->use_index ? ctx->clayer : nullptr;
         key.vals[0] = ctx->c_hits;
         key.vals[1] = ctx->c_events;
         key.vals[2] = threshold;
@@ -1572,6 +1677,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
             int ap_best = 0, ad_best = 0;
             const int32_t epw = events_per_wave(ctx, ctx->c_events);
             ctx->wave_marks = false;  // no host copies here
+            if (ensure_index(ctx)) ctx->use_index = false;
             for (int ap : {1, 2, 4, 8}) {
                 if (ap > ctx->grid.n_phi) continue;
                 for (int ad : {nd, 32, 16, 8}) {

@@ -143,6 +143,40 @@ struct FitParams {
     int32_t nk;
 };
 cudaError_t launch_fit(const FitParams& p, cudaStream_t s);
+// association through a per-(event, layer) angular index (ht_assoc_index.cu)
+struct IndexParams {
+    const float* x;
+    const float* y;
+    const int8_t* layer;
+    const int32_t* offs;
+    int32_t n_events, nl;
+    int32_t* bcount;      // [n_events * nl]
+    int64_t* bstart;      // [n_events * nl + 1]
+    int32_t* bcursor;     // [n_events * nl]
+    uint32_t* r2min;      // [n_events * nl] float bits
+    uint32_t* r2max;
+    float* theta;         // [n_hits] bucket order, sorted by angle within a bucket
+    int32_t* hid;         // [n_hits]
+    int32_t* tab;         // [n_events * nl][257] coarse angle table (positions within the bucket)
+    int64_t* scratch;     // scan scratch
+};
+cudaError_t launch_index_build(const IndexParams& p, cudaStream_t s);
+struct AssocIndexParams {
+    AssocParams a;            // hits, offsets, rows, caps, window, tables, K, stats
+    const ht_peak* peaks;
+    const int64_t* lo_dev;    // the wave's peaks: [*lo_dev, min(*hi_dev, peak_cap))
+    const int64_t* hi_dev;
+    const float* theta;
+    const int32_t* hid;
+    const int32_t* tab;
+    const int64_t* bstart;
+    const uint32_t* r2min;
+    const uint32_t* r2max;
+    int32_t nl;
+    float kmin, dk;           // kappa range start and bin width (float)
+    int32_t* err;             // bit 8: a row came out with another length
+};
+cudaError_t launch_assoc_index(const AssocIndexParams& p, cudaStream_t s);
 // duplicate and mirror merging of fitted candidates (ht_merge.cu)
 struct MergeParams {
     const float* x;
