@@ -431,6 +431,43 @@ def run_gpu(args):
         ms = float(t.item())
     launches = ctx.get_option(ht.HT_OPT_LAUNCHES)
     counts = res.counts.cpu().numpy()
+    # ---- end to end through the C ABI: pinned host inputs and outputs (measured
+    # right after the device steps, before the reports below allocate)
+    if True:  # every rank measures its own end-to-end rate
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hx, hy, ho, hl = pin(batch.x), pin(batch.y), pin(batch.event_offsets), pin(batch.layer)
+        hits_h = ht.Hits.__new__(ht.Hits)
+        hits_h.arrays = (hx, hy, ho, hl)
+        hits_h.struct = ht.HtHits(hx.data_ptr(), hy.data_ptr(), None, hl.data_ptr(), ho.data_ptr(), n_events,
+                                  ht.HT_HOST, n_hits)
+        rh = ht.Results.__new__(ht.Results)
+        rh.peak_cap, rh.pair_cap = res.peak_cap, res.pair_cap
+        rh.peaks = torch.empty((rh.peak_cap, 5), dtype=torch.int32).pin_memory()
+        rh.peak_offsets = torch.empty(rh.peak_cap + 1, dtype=torch.int64).pin_memory()
+        rh.hit_idx = torch.empty(rh.pair_cap, dtype=torch.int32).pin_memory()
+        rh.counts = torch.zeros(2, dtype=torch.int64).pin_memory()
+        rh.struct = ht.HtResults(rh.peaks.data_ptr(), rh.peak_cap, rh.peak_offsets.data_ptr(),
+                                 rh.hit_idx.data_ptr(), rh.pair_cap, rh.counts.data_ptr(), ht.HT_HOST)
+        ectx = ht.Context(g, w.spec.layers)
+        for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
+                     (ht.HT_OPT_THREADS, tile["threads"])):
+            ectx.set_option(k, v)
+        for _ in range(2):  # warm: graph capture, buffers, first DMA into the pinned pages
+            ectx.process(hits_h, w.threshold, w.window, rh, stream)
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ectx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
+            et.append(time.perf_counter() - t0)
+        ectx.close()
+        c = rh.counts.numpy()
+        h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
+        d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
+        e2e = {"value": world * n_events / float(np.mean(et)), "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et))}
+
     # circle fit of the stored candidates of the last step (not in the step)
     fit_ms = []
     for _ in range(3):
@@ -499,42 +536,6 @@ def run_gpu(args):
     plain_ctx.sync(allow_overflow=True)
     plain_eps = psub.n_events / (p0.elapsed_time(p1) / 1e3)
     plain_ctx.close()
-
-    # ---- end to end through the C ABI: pinned host inputs and outputs
-    if True:  # every rank measures its own end-to-end rate
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        hx, hy, ho, hl = pin(batch.x), pin(batch.y), pin(batch.event_offsets), pin(batch.layer)
-        hits_h = ht.Hits.__new__(ht.Hits)
-        hits_h.arrays = (hx, hy, ho, hl)
-        hits_h.struct = ht.HtHits(hx.data_ptr(), hy.data_ptr(), None, hl.data_ptr(), ho.data_ptr(), n_events,
-                                  ht.HT_HOST, n_hits)
-        rh = ht.Results.__new__(ht.Results)
-        rh.peak_cap, rh.pair_cap = res.peak_cap, res.pair_cap
-        rh.peaks = torch.empty((rh.peak_cap, 5), dtype=torch.int32).pin_memory()
-        rh.peak_offsets = torch.empty(rh.peak_cap + 1, dtype=torch.int64).pin_memory()
-        rh.hit_idx = torch.empty(rh.pair_cap, dtype=torch.int32).pin_memory()
-        rh.counts = torch.zeros(2, dtype=torch.int64).pin_memory()
-        rh.struct = ht.HtResults(rh.peaks.data_ptr(), rh.peak_cap, rh.peak_offsets.data_ptr(),
-                                 rh.hit_idx.data_ptr(), rh.pair_cap, rh.counts.data_ptr(), ht.HT_HOST)
-        ectx = ht.Context(g, w.spec.layers)
-        for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
-                     (ht.HT_OPT_THREADS, tile["threads"])):
-            ectx.set_option(k, v)
-        for _ in range(2):  # warm: graph capture, buffers, first DMA into the pinned pages
-            ectx.process(hits_h, w.threshold, w.window, rh, stream)
-        et = []
-        for _ in range(max(1, min(args.steps, 3))):
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ectx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
-            et.append(time.perf_counter() - t0)
-        ectx.close()
-        c = rh.counts.numpy()
-        h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
-        d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
-        e2e = {"value": world * n_events / float(np.mean(et)), "unit": METRIC, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et))}
 
     # ---- serving: continuous batching at two offered loads (rank 0, N=1)
     serving = None
