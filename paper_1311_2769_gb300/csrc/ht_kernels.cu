@@ -681,51 +681,58 @@ __global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const i
     }
 }
 
-// peaks: emission in (event, linear index) order + per-peak pair counts
+// peaks: emission in (event, linear index) order + per-peak pair counts.
+// One lane per column: the column's peaks (few) are walked in bin order;
+// pairs of peaks past the capacity are summed per lane and added once per
+// warp.
 __global__ void emit_kernel(const PeakParams p) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t per_ev = (int64_t)p.nphi * p.nd;
     const int64_t ncols = per_ev * p.n_events;
-    for (int64_t col = gw; col < ncols; col += nwt) {
-        if (p.npk[col] == 0) continue;
-        const int64_t base = p.colbase[col];
-        if (base >= p.peak_cap && p.window < 0) continue;
-        const int e = (int)(col / per_ev);
-        const int ij = (int)(col - e * per_ev);
-        const int i = ij / p.nd;
-        const int j = ij - i * p.nd;
-        const uint32_t* colp = p.acc + (int64_t)e * p.cells + ((int64_t)i * p.nd + j) * p.nk;
-        for (int w = 0; w < p.nkw; ++w) {
-            const unsigned m = p.mask[col * p.nkw + w];
-            if (!m) continue;
-            if (!((m >> lane) & 1u)) continue;
-            const int k = w * 32 + lane;
-            const int64_t pid = base + p.wpre[col * p.nkw + w] + __popc(m & lanemask_lt());
-            if (pid >= p.peak_cap) {
-                if (p.window >= 0 && p.extra_pairs) {
-                    const int lo = max(0, k - p.window), hi = min(p.nk - 1, k + p.window);
-                    unsigned long long s = 0;
-                    for (int kk = lo; kk <= hi; ++kk) s += colp[kk];
-                    atomicAdd(reinterpret_cast<unsigned long long*>(p.extra_pairs), s);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < ncols; c0 += stride) {
+        const int64_t col = c0 + threadIdx.x;
+        unsigned long long extra = 0;
+        const int npk = col < ncols ? p.npk[col] : 0;
+        if (npk > 0) {
+            const int64_t base = p.colbase[col];
+            if (!(base >= p.peak_cap && p.window < 0)) {
+                const int e = (int)(col / per_ev);
+                const int ij = (int)(col - e * per_ev);
+                const int i = ij / p.nd;
+                const int j = ij - i * p.nd;
+                const uint32_t* colp = p.acc + (int64_t)e * p.cells + ((int64_t)i * p.nd + j) * p.nk;
+                int64_t pid = base;
+                for (int w = 0; w < p.nkw; ++w) {
+                    for (unsigned m = p.mask[col * p.nkw + w]; m; m &= m - 1u, ++pid) {
+                        const int k = w * 32 + __ffs(m) - 1;
+                        if (pid >= p.peak_cap) {
+                            if (p.window >= 0 && p.extra_pairs) {
+                                const int lo = max(0, k - p.window), hi = min(p.nk - 1, k + p.window);
+                                for (int kk = lo; kk <= hi; ++kk) extra += colp[kk];
+                            }
+                            continue;
+                        }
+                        ht_peak pk;
+                        pk.event = p.event0 + e;
+                        pk.i_phi = i;
+                        pk.i_d0 = p.line ? k : j;  // line voting runs peaks on the [phi][1][d0] view
+                        pk.i_kappa = p.line ? 0 : k;
+                        pk.votes = colp[k];
+                        p.peaks[pid] = pk;
+                        if (p.window >= 0) {
+                            const int lo = max(0, k - p.window), hi = min(p.nk - 1, k + p.window);
+                            uint32_t s = 0;
+                            for (int kk = lo; kk <= hi; ++kk) s += colp[kk];
+                            p.paircnt[pid] = (int32_t)s;
+                        }
+                    }
                 }
-                continue;
-            }
-            ht_peak pk;
-            pk.event = p.event0 + e;
-            pk.i_phi = i;
-            pk.i_d0 = p.line ? k : j;  // line voting runs peaks on the [phi][1][d0] view
-            pk.i_kappa = p.line ? 0 : k;
-            pk.votes = colp[k];
-            p.peaks[pid] = pk;
-            if (p.window >= 0) {
-                const int lo = max(0, k - p.window), hi = min(p.nk - 1, k + p.window);
-                uint32_t s = 0;
-                for (int kk = lo; kk <= hi; ++kk) s += colp[kk];
-                p.paircnt[pid] = (int32_t)s;
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) extra += __shfl_xor_sync(0xffffffffu, extra, o);
+        if (extra && (threadIdx.x & 31) == 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(p.extra_pairs), extra);
     }
 }
 
@@ -1619,12 +1626,6 @@ cudaError_t launch_order(const int32_t* offs, int32_t event0, int32_t n_events, 
     return cudaGetLastError();
 }
 
-static int warp_grid(int64_t ncols, int threads) {
-    int64_t blocks = (ncols * 32 + threads - 1) / threads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    return blocks < 1 ? 1 : (int)blocks;
-}
-
 // detect tile: R interior rows x TD interior columns, halo included, ~96 KB
 void detect_tile(int nphi, int nd, int nk, int* R, int* TD) {
     const int64_t budget = 96 * 1024 / 4;  // words
@@ -1661,7 +1662,8 @@ cudaError_t launch_detect(const PeakParams& p, cudaStream_t s) {
 cudaError_t launch_emit(const PeakParams& p, cudaStream_t s) {
     const int64_t ncols = (int64_t)p.n_events * p.nphi * p.nd;
     if (ncols == 0) return cudaSuccess;
-    emit_kernel<<<warp_grid(ncols, 256), 256, 0, s>>>(p);
+    const int64_t blocks = (ncols + 255) / 256;
+    emit_kernel<<<(int)std::min<int64_t>(blocks, 152 * 16), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
