@@ -433,7 +433,8 @@ def run_gpu(args):
     counts = res.counts.cpu().numpy()
     # ---- end to end through the C ABI: pinned host inputs and outputs (measured
     # right after the device steps, before the reports below allocate)
-    if True:  # every rank measures its own end-to-end rate
+    e2e = None
+    if not args.no_extras:  # every rank measures its own end-to-end rate
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         hx, hy, ho, hl = pin(batch.x), pin(batch.y), pin(batch.event_offsets), pin(batch.layer)
         hits_h = ht.Hits.__new__(ht.Hits)
@@ -465,8 +466,18 @@ def run_gpu(args):
         c = rh.counts.numpy()
         h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
         d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
+        # the box's pinned device-to-host copy rate (1 GiB into the result
+        # buffer), which bounds this number once the copies overlap compute
+        n_copy = min(1 << 28, rh.pair_cap)
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        rh.hit_idx[:n_copy].copy_(res.hit_idx[:n_copy], non_blocking=True)
+        d1.record(stream)
+        d1.synchronize()
         e2e = {"value": world * n_events / float(np.mean(et)), "unit": METRIC, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et))}
+               "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et)),
+               "d2h_gbs": 4.0 * n_copy / (d0.elapsed_time(d1) * 1e-3) / 1e9}
 
     # circle fit of the stored candidates of the last step (not in the step)
     fit_ms = []
