@@ -50,3 +50,16 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.ht_destroy(None) == -1
     assert lib.ht_sync(None) == -1
     assert lib.ht_create(None, None, None) == -1
+
+
+def test_argument_checks_of_the_extension_calls_need_no_gpu(lib):
+    """Each of these rejects its arguments before any CUDA call."""
+    rate = ctypes.c_double()
+    for kind, iters in ((4, 10), (-1, 10), (0, 0)):
+        assert lib.ht_microbench(kind, iters, ctypes.byref(rate)) == -1
+    assert lib.ht_microbench(0, 10, None) == -1
+    n = ctypes.c_int64()
+    assert lib.ht_fit(None, None, None, 0, None) == -1
+    assert lib.ht_merge(None, None, None, 2, None, 0, ctypes.byref(n), None) == -1
+    assert lib.ht_vertices(None, None, None, 1, None, 0, ctypes.byref(n), None) == -1
+    assert lib.ht_check_rcp(0, 0, None) == -1
