@@ -50,6 +50,24 @@ def _dist():
     return rank, world, local
 
 
+def rank_seed(w, rank):
+    """Generator seed of a rank's batch: rank 0 the workload's own, every
+    other rank its own stream (weak scaling: the same shape, other events)."""
+    return w.seed + 1000 * rank if rank else None
+
+
+def max_over_ranks(x, world, device):
+    """The largest value of a time-like float over the ranks (identity at
+    one rank); `device` is where the process group's backend reduces."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
 
@@ -357,7 +375,7 @@ def run_gpu(args):
     build.build()
     w = synth.WORKLOADS[args.workload]
     g = w.grid
-    batch = synth.generate(w, n_events=args.events, seed=w.seed + 1000 * rank if rank else None)
+    batch = synth.generate(w, n_events=args.events, seed=rank_seed(w, rank))
     n_events, n_hits = batch.n_events, batch.n_hits
     cols = g.n_phi * g.n_d0
     hit_votes = float(n_hits) * cols
@@ -424,11 +442,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
     launches = ctx.get_option(ht.HT_OPT_LAUNCHES)
     counts = res.counts.cpu().numpy()
     # ---- end to end through the C ABI: pinned host inputs and outputs (measured
@@ -475,8 +489,9 @@ def run_gpu(args):
         rh.hit_idx[:n_copy].copy_(res.hit_idx[:n_copy], non_blocking=True)
         d1.record(stream)
         d1.synchronize()
-        e2e = {"value": world * n_events / float(np.mean(et)), "unit": METRIC, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "seconds_per_step": float(np.mean(et)),
+        e2e_s = max_over_ranks(float(np.mean(et)), world, dev)
+        e2e = {"value": world * n_events / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
                "d2h_gbs": 4.0 * n_copy / (d0.elapsed_time(d1) * 1e-3) / 1e9}
 
     # circle fit of the stored candidates of the last step (not in the step)
