@@ -122,7 +122,8 @@ typedef struct {
 #define HT_OPT_THREADS 4           /* threads per vote CTA: 128 or 256 (0 = auto) */
 #define HT_OPT_ACC_BUDGET 5        /* accumulator memory budget in bytes (0 = 40 GB) */
 #define HT_OPT_COUNT_STAGES 6      /* 1 = count precision-stage usage (ht_filter_stats) */
-#define HT_OPT_USE_GRAPH 7         /* 1 = replay the batched step as a CUDA graph (default 1) */
+#define HT_OPT_USE_GRAPH 7         /* 1 = replay the batched step as a CUDA graph (default 1; host
+                                      results copied in chunks, HT_OPT_HOST_CHUNKS > 1, launch directly) */
 #define HT_OPT_PHASE_TIMING 8      /* 1 = time vote / peaks+association with device events */
 #define HT_OPT_LAUNCHES 9          /* read-only: kernels launched by the last ht_process */
 #define HT_OPT_ATILE_PHI 10        /* phi0 rows per association item: 1, 2, 4 or 8 (0 = auto);
