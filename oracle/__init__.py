@@ -61,6 +61,7 @@ def lib():
             "hto_kbin_at": (i32, [G, f, f, f, f, f]),
             "hto_w64": (ctypes.c_double, [G, f, f, f, f, f]),
             "hto_kbin_fp32": (i32, [G, f, f, f, f, f]),
+            "hto_w32": (f, [G, f, f, f, f, f]),
             "hto_kbin_cells": (None, [G, i64, P, P, P, P, P, P]),
             "hto_vote": (None, [G, P, P, P, i32, P]),
             "hto_vote_column": (None, [G, P, P, i64, i32, i32, P]),
@@ -143,6 +144,11 @@ def kbin_cells(g, x, y, c, s, d) -> np.ndarray:
 
 def kbin_fp32(g, x, y, c, s, d) -> int:
     return int(lib().hto_kbin_fp32(ctypes.byref(grid_struct(g)), float(x), float(y), float(c), float(s), float(d)))
+
+
+def w32(g, x, y, c, s, d) -> float:
+    """The float32 op-order bin coordinate (NaN when den <= 0)."""
+    return float(lib().hto_w32(ctypes.byref(grid_struct(g)), float(x), float(y), float(c), float(s), float(d)))
 
 
 def vote(g, x, y, event_offsets=None) -> np.ndarray:

@@ -84,8 +84,9 @@ int32_t hto_kbin(const hto_grid *g, float x, float y, int32_t i, int32_t j)
 
 /* The same formula with float32 operations in a fixed order (IEEE division,
  * no contraction).  Not part of the method's definition: it is the form whose
- * bins are compared against the binary64 ones to report the flip fraction. */
-int32_t hto_kbin_fp32(const hto_grid *g, float x, float y, float c, float s, float d)
+ * bins are compared against the binary64 ones to report the flip fraction.
+ * Returns the float32 bin coordinate w, or NaN when den <= 0. */
+float hto_w32(const hto_grid *g, float x, float y, float c, float s, float d)
 {
     double scale = (double)g->n_kappa / ((double)g->kappa_max - (double)g->kappa_min);
     float S2 = (float)(2.0 * scale);
@@ -96,9 +97,14 @@ int32_t hto_kbin_fp32(const hto_grid *g, float x, float y, float c, float s, flo
     float n = a * S2;
     float den = (r2 + (d * d)) - ((d + d) * q);
     if (!(den > 0.0f))
-        return -1;
+        return NAN;
     float v = n / den;
-    float wv = v + H;
+    return v + H;
+}
+
+int32_t hto_kbin_fp32(const hto_grid *g, float x, float y, float c, float s, float d)
+{
+    float wv = hto_w32(g, x, y, c, s, d);
     if (!(wv >= 0.0f && wv < (float)g->n_kappa))
         return -1;
     return (int32_t)wv;
@@ -263,7 +269,9 @@ typedef struct {
     const hto_grid *g;
     const float *x, *y;
     const int32_t *offs;
-    int32_t n_events, stride, first;
+    const int32_t *order;   /* events in the order they are handed out */
+    int32_t n_events;
+    int32_t *next;          /* shared position in `order` */
     uint32_t threshold;
     int32_t window;
     int64_t votes, peaks, pairs;
@@ -277,7 +285,11 @@ static void *run_worker(void *p)
     uint32_t *acc1 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cells);
     int64_t pcap = 1 << 16;
     hto_peak *pk = (hto_peak *)malloc(sizeof(hto_peak) * (size_t)pcap);
-    for (int32_t e = a->first; e < a->n_events; e += a->stride) {
+    for (;;) {
+        int32_t t = __atomic_fetch_add(a->next, 1, __ATOMIC_RELAXED);
+        if (t >= a->n_events)
+            break;
+        int32_t e = a->order[t];
         int64_t lo = a->offs[e], hi = a->offs[e + 1];
         int32_t offs1[2] = {0, (int32_t)(hi - lo)};
         hto_vote(g, a->x + lo, a->y + lo, offs1, 1, acc1);
@@ -299,16 +311,35 @@ static void *run_worker(void *p)
     return NULL;
 }
 
+/* Events are handed out one at a time from a shared counter, largest event
+ * first (ties by index), so the threads finish together; the per-event work
+ * is the plain single-threaded code above. */
 void hto_run_events(const hto_grid *g, const float *x, const float *y,
                     const int32_t *event_offsets, int32_t n_events,
                     uint32_t threshold, int32_t window, int32_t n_threads, int64_t *out)
 {
     if (n_threads < 1)
         n_threads = 1;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_events > 0 ? n_events : 1));
+    for (int32_t e = 0; e < n_events; ++e) {
+        /* insertion by size, descending (plain; n_events is small) */
+        int32_t t = e;
+        int64_t n = (int64_t)event_offsets[e + 1] - event_offsets[e];
+        while (t > 0) {
+            int32_t o = order[t - 1];
+            int64_t no = (int64_t)event_offsets[o + 1] - event_offsets[o];
+            if (no >= n)
+                break;
+            order[t] = o;
+            --t;
+        }
+        order[t] = e;
+    }
+    int32_t next = 0;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
     run_arg *args = (run_arg *)calloc((size_t)n_threads, sizeof(run_arg));
     for (int32_t t = 0; t < n_threads; ++t) {
-        run_arg a = {g, x, y, event_offsets, n_events, n_threads, t, threshold, window, 0, 0, 0};
+        run_arg a = {g, x, y, event_offsets, order, n_events, &next, threshold, window, 0, 0, 0};
         args[t] = a;
         pthread_create(&th[t], NULL, run_worker, &args[t]);
     }
@@ -321,6 +352,7 @@ void hto_run_events(const hto_grid *g, const float *x, const float *y,
     }
     free(args);
     free(th);
+    free(order);
 }
 
 /* ---- range voting (the first extension beyond the point vote) -------------

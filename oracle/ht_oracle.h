@@ -59,8 +59,10 @@ double hto_w64(const hto_grid *g, float x, float y, float c, float s, float d);
 void hto_kbin_cells(const hto_grid *g, int64_t n, const float *x, const float *y, const float *c,
                     const float *s, const float *d, int32_t *out);
 
-/* Plain float32 op-order bin (IEEE division, no contraction): the form whose
+/* Plain float32 op-order bin coordinate w (IEEE division, no contraction),
+ * NaN when den <= 0, and its bin (-1 when out of range): the form whose
  * disagreement with hto_kbin is reported as the flip fraction. */
+float hto_w32(const hto_grid *g, float x, float y, float c, float s, float d);
 int32_t hto_kbin_fp32(const hto_grid *g, float x, float y, float c, float s, float d);
 
 /* Vote every event: acc is [n_events][n_phi][n_d0][n_kappa] uint32, zeroed here. */
@@ -94,7 +96,8 @@ void hto_flip_count(const hto_grid *g, const float *x, const float *y,
                     const int32_t *event_offsets, int32_t n_events, int64_t *out);
 
 /* Whole path per event (vote, peaks, associate) on n_threads host threads,
- * one event at a time per thread, results reduced to counts:
+ * one event at a time per thread (largest first from a shared counter),
+ * results reduced to counts:
  * out[0] = votes cast, out[1] = peaks, out[2] = pairs.  Used to time the
  * oracle as a CPU baseline. */
 void hto_run_events(const hto_grid *g, const float *x, const float *y,
