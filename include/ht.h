@@ -342,8 +342,11 @@ int ht_filter_stats(ht_ctx *ctx, int64_t *out, int32_t reset);
  * stream capture); every call on a device shares it and starts by clearing
  * what must be zero, so calls that overlap on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  Calls no
- * cudaMalloc/cudaFree.  HT_ERR_INVALID_ARG for a bad grid or pointer,
- * HT_ERR_CUDA if a launch fails. */
+ * cudaMalloc/cudaFree.  Alignment: acc 16-byte aligned when n_kappa is a
+ * multiple of 4 (rows are read with 16-byte loads), else 4-byte; peaks 4-byte,
+ * count 8-byte.  HT_ERR_INVALID_ARG for a bad grid, a NULL or misaligned
+ * pointer, HT_ERR_CUDA if a launch fails.  The kernels' shared-memory limits
+ * are only ever raised, so a call never lowers what a context relies on. */
 #define HT_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ht_peaks_noalloc(const ht_grid *grid, const uint32_t *acc, int32_t n_events, uint32_t threshold,
                      ht_peak *peaks, int64_t cap, int64_t *count, void *stream);

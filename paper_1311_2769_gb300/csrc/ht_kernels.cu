@@ -1500,10 +1500,25 @@ int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant) 
     return table + queues + 4 * tile_phi * tile_d * nk;
 }
 
-
-template <int S>
-static cudaError_t prep_one(int smem) {
-    return cudaFuncSetAttribute(vote_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+// The dynamic shared-memory limit of a kernel is a property of the function,
+// shared by every context and call in the process.  It is only ever raised,
+// to what the device allows beside the kernel's static shared memory, and
+// never set to one call's size: a context (or an allocation-free call) with a
+// smaller tile must not lower the limit that another context's launches rely
+// on.  `smem` is checked against that ceiling.
+static cudaError_t allow_dynamic_smem(const void* f, int smem) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    const int room = optin - (int)fa.sharedSizeBytes;
+    if (smem > room) return cudaErrorInvalidValue;
+    if (fa.maxDynamicSharedSizeBytes >= room) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
 }
 
 template <int S, int N>
@@ -1597,7 +1612,7 @@ cudaError_t launch_finalize(int64_t* scal, cudaStream_t s) {
 cudaError_t vote_prepare(int tile_phi, int nk, int smem, int variant) {
     void* f = vote_variant(tile_phi, nk, variant);
     if (!f) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return allow_dynamic_smem(f, smem);
 }
 
 cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s,
@@ -1645,8 +1660,7 @@ size_t detect_smem(int nphi, int nd, int nk) {
 }
 
 cudaError_t detect_prepare(int nphi, int nd, int nk) {
-    return cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)detect_smem(nphi, nd, nk));
+    return allow_dynamic_smem(reinterpret_cast<const void*>(detect_kernel), (int)detect_smem(nphi, nd, nk));
 }
 
 cudaError_t launch_detect(const PeakParams& p, cudaStream_t s) {
@@ -1709,7 +1723,7 @@ size_t assoc_warp_smem(int rows, int wd, int nk, int cap) { return assoc_warp_by
 cudaError_t assoc_prepare(int tile_phi, int nk, int smem, bool band, int threads, int* blocks_per_sm) {
     void* f = assoc_instance(tile_phi, nk, band);
     if (!f) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem(f, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
@@ -1747,7 +1761,7 @@ cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_s
     int b[2] = {0, 0};
     for (int c = 0; c < 2; ++c) {
         void* f = assoc_range_instance(nk, c != 0, line);
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = allow_dynamic_smem(f, smem);
         if (e != cudaSuccess) return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[c], f, threads, smem);
         if (e != cudaSuccess) return e;

@@ -82,8 +82,16 @@ extern "C" int ht_peaks_noalloc(const ht_grid* grid, const uint32_t* acc, int32_
                                 ht_peak* peaks, int64_t cap, int64_t* count, void* stream) {
     if (!grid_valid(grid) || !acc || n_events < 0 || !count || cap < 0 || (cap > 0 && !peaks))
         return HT_ERR_INVALID_ARG;
+    // the detection stages whole kappa rows with 16-byte loads when n_kappa is
+    // a multiple of 4; the count is one 8-byte store, the peaks 4-byte fields
+    if (((uintptr_t)count & 7u) != 0 || ((uintptr_t)peaks & 3u) != 0 || ((uintptr_t)acc & 3u) != 0 ||
+        (grid->n_kappa % 4 == 0 && ((uintptr_t)acc & 15u) != 0))
+        return HT_ERR_INVALID_ARG;
     const int nkw = (grid->n_kappa + 31) / 32;
     const int64_t cols = (int64_t)n_events * grid->n_phi * grid->n_d0;
+    // each column takes 12 + 6 nkw bytes of scratch (count, base, mask, word
+    // prefixes): refuse before the layout's size arithmetic could wrap
+    if (cols > (int64_t)(HT_NOALLOC_SCRATCH_BYTES / (12u + 6u * (unsigned)nkw))) return HT_ERR_BUDGET;
     const Layout L = layout(cols, nkw);
     if (L.total > (size_t)HT_NOALLOC_SCRATCH_BYTES) return HT_ERR_BUDGET;
     if (detect_smem(grid->n_phi, grid->n_d0, grid->n_kappa) > 227 * 1024) return HT_ERR_INVALID_ARG;

@@ -370,7 +370,18 @@ def ht_phase_times(ctx):
 
 def ht_peaks_noalloc(grid, acc, n_events, threshold, peaks, cap, count, stream=None):
     """Peaks of device accumulators with no device allocation (see ht.h).
-    acc, peaks (int32 [cap, 5]) and count (int64 [1]) are CUDA tensors."""
+    acc (uint32 or int32, at least n_events * cells elements), peaks (int32,
+    at least 5 * cap elements) and count (int64) are contiguous CUDA tensors
+    on the current device."""
+    cells = int(grid.n_phi) * int(grid.n_d0) * int(grid.n_kappa)
+    for name, t, dtypes, need in (("acc", acc, ("int32", "uint32"), int(n_events) * cells),
+                                  ("peaks", peaks, ("int32",), 5 * int(cap)), ("count", count, ("int64",), 1)):
+        if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+            raise ValueError(f"ht_peaks_noalloc: {name} must be a contiguous CUDA tensor")
+        if str(t.dtype).replace("torch.", "") not in dtypes:
+            raise ValueError(f"ht_peaks_noalloc: {name} must be {' or '.join(dtypes)}, not {t.dtype}")
+        if t.numel() < need:
+            raise ValueError(f"ht_peaks_noalloc: {name} holds {t.numel()} elements, {need} needed")
     g = HtGrid(int(grid.n_phi), int(grid.n_d0), int(grid.n_kappa), float(grid.d0_min), float(grid.d0_max),
                float(grid.kappa_min), float(grid.kappa_max))
     return _check(load().ht_peaks_noalloc(ctypes.byref(g), _ptr(acc), int(n_events), int(threshold), _ptr(peaks),

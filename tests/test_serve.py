@@ -82,7 +82,7 @@ def test_admission_waits_for_memory():
 
 
 @pytest.mark.gpu
-def test_result_same_alone_and_in_the_mix():
+def test_result_same_alone_and_in_the_mix(oracle_mod):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -119,3 +119,19 @@ def test_result_same_alone_and_in_the_mix():
         assert np.array_equal(peaks, want)
         assert np.array_equal(offsets, po) and np.array_equal(hits, hi)
         assert done[eid][0].n_peaks == len(pk) and done[eid][0].n_pairs == len(hi)
+    # the served results against the oracle (events of at most 6000 hits
+    # keep the single-threaded oracle quick)
+    checked = 0
+    for eid in sorted(sample):
+        e = evs[eid]
+        if len(e.x) > 6000:
+            continue
+        acc = oracle_mod.vote(w.grid, e.x, e.y)
+        opk = oracle_mod.peaks(w.grid, acc, w.threshold)
+        opo, ohi = oracle_mod.associate(w.grid, e.x, e.y, None, opk, w.window)
+        peaks, offsets, hits = kept[eid]
+        want = np.stack([opk["i_phi"], opk["i_d0"], opk["i_kappa"], opk["votes"].astype(np.int32)], 1)
+        assert np.array_equal(peaks, want)
+        assert np.array_equal(offsets, opo) and np.array_equal(hits, ohi)
+        checked += 1
+    assert checked >= 6
