@@ -151,6 +151,18 @@ typedef struct {
                                       curvature can fall in a peak's window (needs layer ids and at
                                       most 32 layers); 0 (default): every hit in every column.  Same
                                       rows either way. */
+#define HT_OPT_RECORDS 17          /* 1 (default): in ht_process the band vote also writes, for every
+                                      hit whose d0 band meets a tile, the tile's bins (one byte per
+                                      cell) and the association reads them instead of binning every
+                                      cell again; used with point voting, band pruning of the vote,
+                                      n_kappa <= 255 and a vote tile of 32, 64, 128 or 256 cells
+                                      (other cases, and 0, bin again).  Same rows either way. */
+#define HT_OPT_RECORD_BUDGET 18    /* device memory for those records in bytes (0 = 72 GB): a wave of
+                                      events needs (its hits) x (vote tiles per event) x (cells per
+                                      tile) bytes, and ht_process splits the batch into waves that fit
+                                      (for device hits whose records exceed it, the event offsets are
+                                      read back once, synchronously); an event too large for it alone
+                                      is binned again instead. */
 
 /* Vote modes.  HT_VOTE_POINT: a hit votes, in each (phi0, d0) column, for the
  * kappa bin of its curve at the column's centre (Section 3's vote, point

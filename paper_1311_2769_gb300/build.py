@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libht.so")
-SOURCES = ["ht_kernels.cu", "ht_api.cu", "ht_noalloc.cu", "ht_fit.cu", "ht_vertex.cu", "ht_merge.cu", "ht_microbench.cu", "ht_assoc_index.cu"]
+SOURCES = ["ht_kernels.cu", "ht_api.cu", "ht_noalloc.cu", "ht_fit.cu", "ht_vertex.cu", "ht_merge.cu", "ht_microbench.cu",
+           "ht_assoc_index.cu", "ht_assoc_rec.cu"]
 HEADERS = ["ht_kbin.cuh", "ht_internal.h"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -22,12 +22,12 @@ struct DBuf {
     size_t n = 0;
     // Grow to at least `want` elements (contents are not preserved).  Bumps *gen
     // on reallocation so captured graphs that hold the old pointer are dropped.
-    cudaError_t ensure(size_t want, int* gen) {
+    cudaError_t ensure(size_t want, int* gen, bool slack = true) {
         if (want <= n && p) return cudaSuccess;
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
-        size_t alloc = want + want / 4 + 16;
+        size_t alloc = slack ? want + want / 4 + 16 : want;
         cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), alloc * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
@@ -47,13 +47,15 @@ struct DBuf {
 
 struct GraphKey {
     const void* ptrs[8];
-    int64_t vals[12];
+    int64_t vals[13];
     bool operator==(const GraphKey& o) const {
         return std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && std::memcmp(vals, o.vals, sizeof(vals)) == 0;
     }
 };
 
 constexpr int64_t kDefaultBudget = 40LL << 30;
+constexpr int64_t kDefaultRecBudget = 72LL << 30;
+constexpr size_t kRecWarpBudget = 12288;  // shared memory per warp of the record association
 
 }  // namespace
 
@@ -105,6 +107,19 @@ struct ht_ctx {
     int r_variant = 0;  // vote kernel: 0 full sweep, 1 band compaction, 2 range
     int a_tile_phi = 1, a_tile_d = 1, a_threads = 256, a_cap = 0, a_blocks_per_sm = 1;  // association item
     size_t a_warp_bytes = 0;
+    // association over vote records (items are the vote's tiles)
+    int records = 1;
+    int64_t rec_budget = kDefaultRecBudget;
+    bool r_rec = false;                    // the resolved vote tile supports records
+    int r_rec_blocks_per_sm = 1;           // the record-writing vote's occupancy
+    int rc_threads = 128, rc_cap = 256, rc_blocks_per_sm = 1;
+    size_t rc_warp_bytes = 0;
+    bool use_rec = false;                  // the current ht_process associates through records
+    std::vector<int32_t> wave_start;       // the current ht_process's waves: first events, then c_events
+    std::vector<int32_t> h_offs;           // host copy of device event offsets (wave planning)
+    std::vector<int32_t> gwaves;           // the wave plan the captured graph was made with
+    DBuf<uint8_t> rec;
+    DBuf<uint32_t> rbits;
 
     int gen = 0;  // buffer generation (graph invalidation)
     DBuf<float> sx, sy;
@@ -168,7 +183,9 @@ struct ht_ctx {
 
     // optional per-phase device timing (external events, also inside graphs)
     bool timing = false;
-    cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // five per wave: vote start, vote end, association end, step end, association start
+    std::vector<cudaEvent_t> tev;
+    int tev_waves = 0;  // waves timed by the last ht_process
     float phase_ms[4] = {0, 0, 0, 0};
     int64_t launches = 0;  // kernels issued by the last ht_process
 
@@ -338,6 +355,33 @@ int resolve_tiles(ht_ctx* ctx) {
     ctx->r_threads = thr;
     ctx->r_smem = smem;
     ctx->r_blocks_per_sm = per_sm;
+    // records: the band vote writes each tile's bins, the association reads them
+    ctx->r_rec = false;
+    if (ctx->records && variant == 1 && ctx->vote_mode == HT_VOTE_POINT && assoc_rec_supported(tp, td, nk)) {
+        int rper = 0;
+        CU(vote_prepare(tp, nk, smem, 3));
+        CU(vote_occupancy(tp, nk, thr, smem, &rper, 3));
+        // row cursors: about four peaks per cell before a tile needs a second
+        // pass over its records (the batch workload averages under two)
+        const size_t fixed = assoc_rec_warp_smem(tp, td, nk, 0);
+        int cap = fixed + 8 * 64 <= kRecWarpBudget ? (int)((kRecWarpBudget - fixed) / 8) & ~31 : 64;
+        cap = std::max(cap, std::min(4 * tp * td, 1024));
+        cap = ctx->acap > 0 ? ctx->acap : std::min(std::max(cap, 64), 1024);
+        const size_t wbytes = assoc_rec_warp_smem(tp, td, nk, cap);
+        const int athr_r = 128;
+        int ablocks = 0;
+        if (rper >= 1 && wbytes * (athr_r / 32) <= 227 * 1024 &&
+            assoc_rec_prepare(tp, td, nk, (int)(wbytes * (athr_r / 32)), athr_r, &ablocks) == cudaSuccess &&
+            ablocks >= 1) {
+            ctx->r_rec = true;
+            ctx->r_rec_blocks_per_sm = rper;
+            ctx->rc_threads = athr_r;
+            ctx->rc_cap = cap;
+            ctx->rc_warp_bytes = wbytes;
+            ctx->rc_blocks_per_sm = ablocks;
+        }
+        cudaGetLastError();
+    }
     // association items: a_tile_phi rows x a_tile_d d0 columns, at most 32
     // columns, several rows only over all d0 columns (so an item's peaks are
     // consecutive).  Per warp: the d0 table, the item's peak tables and row
@@ -553,10 +597,26 @@ VoteParams vote_params(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent)
     return p;
 }
 
-// Vote events [event0, event0 + ne) of the staged batch into acc[0..ne).
+// Vote records per hit of the batch: one record per vote tile of its event.
+int64_t rec_per_hit(const ht_ctx* ctx) {
+    const int64_t tiles = (int64_t)((ctx->grid.n_phi + ctx->r_tile_phi - 1) / ctx->r_tile_phi) *
+                          ((ctx->grid.n_d0 + ctx->r_tile_d - 1) / ctx->r_tile_d);
+    return tiles * ctx->r_tile_phi * ctx->r_tile_d;
+}
+
+// Vote events [event0, event0 + ne) of the staged batch into acc[0..ne)
+// (and, with ctx->use_rec, their records).
 int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStream_t s) {
     if (ne <= 0) return HT_OK;
     VoteParams p = vote_params(ctx, event0, ne, persistent);
+    int variant = ctx->r_variant, per_sm = ctx->r_blocks_per_sm;
+    if (ctx->use_rec && ctx->vote_mode == HT_VOTE_POINT) {
+        p.rec = ctx->rec.p;
+        p.rbits = ctx->rbits.p;
+        p.rec_bytes = ctx->r_tile_phi * ctx->r_tile_d;
+        variant = 3;
+        per_sm = ctx->r_rec_blocks_per_sm;
+    }
     if (ctx->vote_mode == HT_VOTE_LINE) {
         if (persistent) CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
         CU(cudaMemsetAsync(ctx->acc.p, 0, (size_t)ne * ctx->cells * sizeof(uint32_t), s));
@@ -566,10 +626,10 @@ int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStrea
     if (persistent) {
         CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
         CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), s));
-        const int grid = std::min<int64_t>(p.n_items, (int64_t)ctx->sms * ctx->r_blocks_per_sm);
-        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s, ctx->r_variant));
+        const int grid = std::min<int64_t>(p.n_items, (int64_t)ctx->sms * per_sm);
+        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s, variant));
     } else {
-        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, ctx->r_variant));
+        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, variant));
     }
     return HT_OK;
 }
@@ -652,6 +712,23 @@ int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, co
         a.line_d0min = (double)ctx->grid.d0_min;
         a.line_d0max = (double)ctx->grid.d0_max;
     }
+    if (pass == 0 && ctx->use_rec) {
+        a.rec = ctx->rec.p;
+        a.rbits = ctx->rbits.p;
+        a.rec_bytes = ctx->r_tile_phi * ctx->r_tile_d;
+        a.rtiles_phi = (ctx->grid.n_phi + ctx->r_tile_phi - 1) / ctx->r_tile_phi;
+        a.rtiles_d = (ctx->grid.n_d0 + ctx->r_tile_d - 1) / ctx->r_tile_d;
+        a.rtile_d = ctx->r_tile_d;
+        a.cap = ctx->rc_cap;
+        a.warp_bytes = ctx->rc_warp_bytes;
+        const int64_t items = (int64_t)ne * a.rtiles_phi * a.rtiles_d;
+        const int warps = ctx->rc_threads / 32;
+        const int grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>((items + warps - 1) / warps, (int64_t)ctx->sms * ctx->rc_blocks_per_sm));
+        CU(cudaMemsetAsync(ctx->d_aqueue, 0, sizeof(unsigned long long), s));
+        CU(launch_assoc_rec(a, ctx->r_tile_phi, ctx->rc_threads, grid, s));
+        return HT_OK;
+    }
     const int64_t items = (int64_t)ne * ((ctx->grid.n_phi + ctx->a_tile_phi - 1) / ctx->a_tile_phi) *
                           ((ctx->pnd + ctx->a_tile_d - 1) / ctx->a_tile_d);
     const int warps = ctx->a_threads / 32;
@@ -666,10 +743,10 @@ int launch_assoc_ctx(ht_ctx* ctx, AssocParams& a, int32_t event0, int32_t ne, co
 }
 
 // pair offsets for this wave's peaks [d_scal[2], d_scal[0]) clamped to cap, and association
-int mark(ht_ctx* ctx, int which, cudaStream_t s);
+int mark(ht_ctx* ctx, int wi, int which, cudaStream_t s);
 
 int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* order, int64_t peak_cap,
-                    int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, bool timed,
+                    int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t window, int wave_timed,
                     cudaStream_t s) {
     const bool range = ctx->vote_mode != HT_VOTE_POINT;
     if (range) {
@@ -701,11 +778,11 @@ int run_pairs_assoc(ht_ctx* ctx, int32_t event0, int32_t ne, const int32_t* orde
     a.hit_idx = hit_idx;
     a.pair_cap = pair_cap;
     a.window = window;
-    if (timed) {
-        const int st = mark(ctx, 4, s);
+    if (wave_timed >= 0) {
+        const int st = mark(ctx, wave_timed, 4, s);
         if (st) return st;
     }
-    if (!range && ctx->use_index) {
+    if (!range && ctx->use_index && !ctx->use_rec) {
         AssocIndexParams q{};
         q.a = a;
         q.a.x = ctx->cx;
@@ -757,49 +834,128 @@ int32_t events_per_wave(ht_ctx* ctx, int32_t n_events) {
 }
 
 // Device work of ht_process for the staged batch (graph-capturable).
-// Records one of the phase events (external, so it also works inside a graph).
-int mark(ht_ctx* ctx, int which, cudaStream_t s) {
-    if (ctx->timing) CU(cudaEventRecordWithFlags(ctx->tev[which], s, cudaEventRecordExternal));
+// Records one of wave wi's phase events (external, so it also works inside a graph).
+int mark(ht_ctx* ctx, int wi, int which, cudaStream_t s) {
+    if (ctx->timing && (size_t)(5 * wi + which) < ctx->tev.size())
+        CU(cudaEventRecordWithFlags(ctx->tev[5 * wi + which], s, cudaEventRecordExternal));
+    return HT_OK;
+}
+
+// Phase events for n waves (created before any capture).
+int ensure_timing_events(ht_ctx* ctx, int n) {
+    while ((int)ctx->tev.size() < 5 * std::max(n, 1)) {
+        cudaEvent_t e = nullptr;
+        CU(cudaEventCreate(&e));
+        ctx->tev.push_back(e);
+    }
+    return HT_OK;
+}
+
+// The waves of the staged batch: at most `step` events each and, when the
+// association reads vote records, at most rec_budget bytes of records each.
+// The events' sizes are needed only when the whole batch's records exceed the
+// budget; device offsets are then read back once (synchronously).  An event
+// whose records alone exceed the budget turns records off for the call.  The
+// record buffers are sized for the largest wave.
+int plan_waves(ht_ctx* ctx, const ht_hits* hits, int32_t step, cudaStream_t s) {
+    std::vector<int32_t>& w = ctx->wave_start;
+    w.clear();
+    const int32_t ne = ctx->c_events;
+    step = std::max<int32_t>(step, 1);
+    ctx->use_rec = ctx->r_rec && ctx->vote_mode == HT_VOTE_POINT && ctx->c_hits > 0 && ne > 0;
+    const int64_t rph = ctx->use_rec ? rec_per_hit(ctx) : 0;
+    const int64_t hits_fit = rph > 0 ? ctx->rec_budget / rph : 0;  // hits whose records fit the budget
+    int64_t max_hits = ctx->c_hits;
+    int32_t max_ne = std::min(step, ne);
+    const bool by_size = ctx->use_rec && ctx->c_hits > hits_fit;
+    if (by_size) {
+        const int32_t* o = nullptr;
+        if (hits && hits->mem == HT_HOST) {
+            o = hits->event_offsets;
+        } else {
+            ctx->h_offs.resize((size_t)ne + 1);
+            CU(cudaMemcpyAsync(ctx->h_offs.data(), ctx->coffs, ((size_t)ne + 1) * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            o = ctx->h_offs.data();
+            if (o[0] != 0 || (int64_t)o[ne] != ctx->c_hits)
+                return fail(ctx, HT_ERR_INVALID_ARG, "event_offsets must start at 0 and end at n_hits");
+            for (int32_t e = 0; e < ne; ++e)
+                if (o[e] > o[e + 1]) return fail(ctx, HT_ERR_INVALID_ARG, "event_offsets decrease at event %d", e);
+        }
+        max_hits = 0;
+        max_ne = 0;
+        for (int32_t e = 0; e < ne;) {
+            const int32_t e0 = e;
+            int64_t h = 0;
+            while (e < ne && e - e0 < step) {
+                const int64_t he = (int64_t)o[e + 1] - o[e];
+                if (e > e0 && h + he > hits_fit) break;
+                h += he;
+                ++e;
+            }
+            if (h > hits_fit) {  // one event alone exceeds the budget
+                ctx->use_rec = false;
+                break;
+            }
+            w.push_back(e0);
+            max_hits = std::max(max_hits, h);
+            max_ne = std::max(max_ne, e - e0);
+        }
+    }
+    if (!by_size || !ctx->use_rec) {
+        w.clear();
+        for (int32_t e = 0; e < ne; e += step) w.push_back(e);
+        max_hits = ctx->c_hits;
+        max_ne = std::min(step, ne);
+    }
+    w.push_back(ne);
+    if (ctx->use_rec) {
+        const int64_t tiles = rph / ((int64_t)ctx->r_tile_phi * ctx->r_tile_d);
+        CU(ctx->rec.ensure((size_t)std::max<int64_t>(1, max_hits * rph), &ctx->gen, false));
+        CU(ctx->rbits.ensure((size_t)std::max<int64_t>(1, ((max_hits >> 5) + max_ne + 1) * tiles), &ctx->gen));
+    }
     return HT_OK;
 }
 
 int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, int64_t peak_cap,
-                   int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, int32_t epw, cudaStream_t s) {
+                   int64_t* peak_offsets, int32_t* hit_idx, int64_t pair_cap, cudaStream_t s) {
     CU(cudaMemsetAsync(ctx->d_scal, 0, 8 * sizeof(int64_t), s));
     const bool plain = ctx->mode == HT_MODE_PLAIN;
-    const int32_t step = plain ? 1 : epw;
     // kernels per wave: [order] vote, detect, scan x3, emit, scan x3, assoc
     ctx->launches = 1;  // finalize
     int st = HT_OK;
     ctx->cur_peaks = peaks;
-    if (ctx->use_index) {  // count, scan x3, scatter, sort
+    if (ctx->use_index && !ctx->use_rec) {  // count, scan x3, scatter, sort
         if ((st = build_index(ctx, s))) return st;
         ctx->launches += 6;
     }
-    const bool single = ctx->c_events <= step;  // phase timing needs one wave
-    for (int32_t e0 = 0; e0 < ctx->c_events; e0 += step) {
-        const int32_t ne = std::min(step, ctx->c_events - e0);
-        if (single && (st = mark(ctx, 0, s))) return st;
+    const std::vector<int32_t>& waves = ctx->wave_start;
+    const int nwaves = waves.empty() ? 0 : (int)waves.size() - 1;
+    ctx->tev_waves = ctx->timing ? std::min<int>(nwaves, (int)ctx->tev.size() / 5) : 0;
+    for (int wi = 0; wi < nwaves; ++wi) {
+        const int32_t e0 = waves[wi];
+        const int32_t ne = waves[wi + 1] - e0;
+        if ((st = mark(ctx, wi, 0, s))) return st;
         st = run_vote(ctx, e0, ne, !plain, s);
         if (st) return st;
-        if (single && (st = mark(ctx, 1, s))) return st;
+        if ((st = mark(ctx, wi, 1, s))) return st;
         // range voting counts rows in the association (window sums over-count)
         PeakParams pp = peak_params(ctx, e0, ne, thr, peaks, peak_cap, ctx->vote_mode != HT_VOTE_POINT ? -1 : window);
         st = run_detect_scan(ctx, pp, s);
         if (st) return st;
         CU(launch_emit(pp, s));
         st = run_pairs_assoc(ctx, e0, ne, plain ? nullptr : ctx->order.p, peak_cap, peak_offsets, hit_idx, pair_cap,
-                             window, single, s);
+                             window, wi, s);
         if (st) return st;
-        if (single && (st = mark(ctx, 2, s))) return st;
+        if ((st = mark(ctx, wi, 2, s))) return st;
         if (ctx->wave_marks) {  // running totals after this wave, then its event (host copies follow it)
-            const int wi = e0 / step;
             CU(cudaMemcpyAsync(ctx->h_wave + 2 * wi, ctx->d_scal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             CU(cudaEventRecord(ctx->wave_ev[wi], s));
         }
         ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode != HT_VOTE_POINT ? 1 : 0);
     }
-    if (single && (st = mark(ctx, 3, s))) return st;
+    if (nwaves > 0 && (st = mark(ctx, nwaves - 1, 3, s))) return st;
     if (ctx->c_events == 0 && peak_offsets && peak_cap >= 0)
         CU(cudaMemsetAsync(peak_offsets, 0, sizeof(int64_t), s));
     CU(launch_finalize(ctx->d_scal, s));
@@ -1029,6 +1185,14 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             ctx->assoc_index = (int)value;
             ctx->gvalid = false;
             break;
+        case HT_OPT_RECORDS:
+            if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "records must be 0 or 1");
+            ctx->records = (int)value;
+            break;
+        case HT_OPT_RECORD_BUDGET:
+            if (value < 0) return fail(ctx, HT_ERR_INVALID_ARG, "record budget < 0");
+            ctx->rec_budget = value ? value : kDefaultRecBudget;
+            break;
         case HT_OPT_VOTE_MODE: {
             if (value != HT_VOTE_POINT && value != HT_VOTE_RANGE && value != HT_VOTE_LINE)
                 return fail(ctx, HT_ERR_INVALID_ARG, "vote mode must be HT_VOTE_POINT, HT_VOTE_RANGE or HT_VOTE_LINE");
@@ -1052,15 +1216,18 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             break;
         }
         case HT_OPT_PHASE_TIMING:
-            if (value && !ctx->tev[0])
-                for (auto& e : ctx->tev) CU(cudaEventCreate(&e));
+            if (value) {
+                const int st = ensure_timing_events(ctx, 1);
+                if (st) return st;
+            }
             ctx->timing = value != 0;
             break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
     ctx->gvalid = false;
     if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS || key == HT_OPT_ATILE_PHI ||
-        key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE || key == HT_OPT_VOTE_MODE || key == HT_OPT_ASSOC_CURSORS) {
+        key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE || key == HT_OPT_VOTE_MODE || key == HT_OPT_ASSOC_CURSORS ||
+        key == HT_OPT_RECORDS) {
         int st = resolve_tiles(ctx);
         if (st) return st;
     }
@@ -1082,10 +1249,12 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_PRUNE: *value = (ctx->r_band ? 1 : 0) | (ctx->a_band ? 2 : 0); break;
         case HT_OPT_ATILE_D0: *value = ctx->a_tile_d; break;
         case HT_OPT_VOTE_MODE: *value = ctx->vote_mode; break;
-        case HT_OPT_ASSOC_CURSORS: *value = ctx->a_cap; break;
+        case HT_OPT_ASSOC_CURSORS: *value = ctx->r_rec ? ctx->rc_cap : ctx->a_cap; break;
         case HT_OPT_HOST_CHUNKS: *value = ctx->host_chunks; break;
         case HT_OPT_ASSOC_INDEX: *value = ctx->assoc_index; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
+        case HT_OPT_RECORDS: *value = ctx->r_rec ? 1 : 0; break;
+        case HT_OPT_RECORD_BUDGET: *value = ctx->rec_budget; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
     }
     return HT_OK;
@@ -1102,6 +1271,7 @@ int ht_vote(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     if (st) return st;
     ctx->stream = s;
     ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
+    ctx->use_rec = false;  // the separate calls bin again in ht_associate
     st = ensure_wave_buffers(ctx, ctx->c_events);
     if (st) return st;
     const bool plain = ctx->mode == HT_MODE_PLAIN;
@@ -1245,7 +1415,13 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
                       ctx->c_events > 1;
     int32_t step = epw;
     if (pipe) step = std::min<int32_t>(epw, (ctx->c_events + ctx->host_chunks - 1) / ctx->host_chunks);
-    const int32_t nwaves = ctx->c_events > 0 ? (ctx->c_events + step - 1) / step : 0;
+    st = plan_waves(ctx, hits, ctx->mode == HT_MODE_PLAIN ? 1 : step, s);
+    if (st) return st;
+    const int32_t nwaves = (int32_t)ctx->wave_start.size() - 1;
+    if (ctx->timing) {
+        st = ensure_timing_events(ctx, nwaves);
+        if (st) return st;
+    }
     ctx->wave_marks = pipe;
     if (pipe) {
         while ((int32_t)ctx->wave_ev.size() < nwaves) {
@@ -1288,7 +1464,8 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         key.vals[10] = ctx->count_stages * 2 + ctx->timing;
         key.vals[11] = ((int64_t)ctx->a_tile_phi << 40) | ((int64_t)ctx->a_tile_d << 20) | ((int64_t)ctx->a_cap << 2) |
                        (ctx->r_band ? 2 : 0) | (ctx->a_band ? 1 : 0) | ((int64_t)ctx->vote_mode << 60);
-        if (!ctx->gvalid || !(key == ctx->gkey)) {
+        key.vals[12] = (ctx->use_rec ? 1 : 0) | ((int64_t)ctx->rc_cap << 1);
+        if (!ctx->gvalid || !(key == ctx->gkey) || ctx->gwaves != ctx->wave_start) {
             if (ctx->gexec) {
                 cudaGraphExecDestroy(ctx->gexec);
                 ctx->gexec = nullptr;
@@ -1296,7 +1473,7 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
             ctx->gvalid = false;
             cudaGraph_t g = nullptr;
             CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, step, s);
+            st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, s);
             cudaError_t ce = cudaStreamEndCapture(s, &g);
             if (st) {
                 if (g) cudaGraphDestroy(g);
@@ -1307,11 +1484,12 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
             cudaGraphDestroy(g);
             CU(ie);
             ctx->gkey = key;
+            ctx->gwaves = ctx->wave_start;
             ctx->gvalid = true;
         }
         CU(cudaGraphLaunch(ctx->gexec, s));
     } else {
-        st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, step, s);
+        st = process_device(ctx, threshold, window, peaks, pcap, poff, hidx, qcap, s);
         if (st) return st;
     }
     ctx->have_results = true;
@@ -1373,13 +1551,20 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
 int ht_sync(ht_ctx* ctx) {
     if (!ctx) return HT_ERR_INVALID_ARG;
     CU(cudaStreamSynchronize(ctx->stream));
-    if (ctx->timing && ctx->c_events > 0) {
-        float ms = 0;
-        if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[1]) == cudaSuccess) ctx->phase_ms[0] = ms;
-        if (cudaEventElapsedTime(&ms, ctx->tev[1], ctx->tev[2]) == cudaSuccess) ctx->phase_ms[1] = ms;
-        if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[3]) == cudaSuccess) ctx->phase_ms[2] = ms;
-        if (cudaEventElapsedTime(&ms, ctx->tev[4], ctx->tev[2]) == cudaSuccess) ctx->phase_ms[3] = ms;
+    if (ctx->timing && ctx->c_events > 0 && ctx->tev_waves > 0) {
+        // vote, peaks + association and association summed over the waves;
+        // the whole step from the first wave's start to the end
+        float sum[4] = {0, 0, 0, 0}, ms = 0;
+        const int nw = ctx->tev_waves;
+        for (int w = 0; w < nw; ++w) {
+            const cudaEvent_t* t = ctx->tev.data() + 5 * w;
+            if (cudaEventElapsedTime(&ms, t[0], t[1]) == cudaSuccess) sum[0] += ms;
+            if (cudaEventElapsedTime(&ms, t[1], t[2]) == cudaSuccess) sum[1] += ms;
+            if (cudaEventElapsedTime(&ms, t[4], t[2]) == cudaSuccess) sum[3] += ms;
+        }
+        if (cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[5 * (nw - 1) + 3]) == cudaSuccess) sum[2] = ms;
         cudaGetLastError();
+        for (int i = 0; i < 4; ++i) ctx->phase_ms[i] = sum[i];
     }
     int st = read_err(ctx);
     if (st) return st;
@@ -1617,11 +1802,75 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
     std::vector<int> tds;
     for (int td : {nd, 128, 64, 32, 16, 8})
         if (td <= nd && std::find(tds.begin(), tds.end(), td) == tds.end()) tds.push_back(td);
+    // With records, the tile also decides the association's items and record
+    // size: time the whole step (vote, peaks, association; threshold 9,
+    // window 1, the batch workload's reading) over the tiles that support
+    // records, and keep the fastest.
+    if (ctx->records && ctx->vote_mode == HT_VOTE_POINT && (ctx->prune & 1) && ctx->K.band_ok && nk <= 255) {
+        DBuf<ht_peak> pk;
+        DBuf<int64_t> po;
+        DBuf<int32_t> hi;
+        const int64_t pcap = std::min<int64_t>(ctx->cells * ctx->c_events / 8 + 1024, 1LL << 27);
+        const int64_t qcap = std::min<int64_t>(pcap * 64, 1LL << 31);
+        float rbest = 1e30f;
+        int rp = 0, rd = 0, rt = 0;
+        if (pk.ensure(pcap, nullptr) == cudaSuccess && po.ensure(pcap + 1, nullptr) == cudaSuccess &&
+            hi.ensure(qcap, nullptr) == cudaSuccess && ctx->paircnt.ensure(pcap, &ctx->gen) == cudaSuccess) {
+            const bool timing = ctx->timing;
+            const int32_t epw = events_per_wave(ctx, ctx->c_events);
+            ctx->wave_marks = false;
+            ctx->timing = true;
+            for (int tp : {1, 2, 4, 8}) {
+                if (tp > ctx->grid.n_phi) continue;
+                for (int td : tds) {
+                    if (!assoc_rec_supported(tp, td, nk)) continue;
+                    const int smem = vote_smem_bytes(tp, td, nk, 256, 3);
+                    if (smem > 200 * 1024) continue;
+                    for (int thr : {128, 256}) {
+                        ctx->tile_phi = tp;
+                        ctx->tile_d = td;
+                        ctx->threads = thr;
+                        if (resolve_tiles(ctx) || !ctx->r_rec) continue;
+                        if (plan_waves(ctx, hits, epw, s) || ensure_timing_events(ctx, (int)ctx->wave_start.size() - 1))
+                            continue;
+                        if (process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s)) continue;  // warm
+                        if (process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s)) continue;
+                        CU(cudaStreamSynchronize(s));
+                        float ms = 0;
+                        const int nw = ctx->tev_waves;
+                        if (nw < 1 || cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[5 * (nw - 1) + 3]) != cudaSuccess) {
+                            cudaGetLastError();
+                            continue;
+                        }
+                        if (ms < rbest) {
+                            rbest = ms;
+                            rp = tp;
+                            rd = td;
+                            rt = thr;
+                        }
+                    }
+                }
+            }
+            ctx->timing = timing;
+        }
+        pk.release();
+        po.release();
+        hi.release();
+        if (rp) {
+            ctx->tile_phi = rp;
+            ctx->tile_d = rd;
+            ctx->threads = rt;
+            ctx->gvalid = false;
+            ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
+            return resolve_tiles(ctx);
+        }
+    }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
     int bp = 0, bd = 0, bt = 0;
+    ctx->use_rec = false;
     for (int tp : {1, 2, 4, 8}) {
         if (tp > ctx->grid.n_phi) continue;
         for (int td : tds) {
@@ -1687,11 +1936,12 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
                     if (resolve_tiles(ctx)) continue;
                     if (ctx->a_tile_d != ad) continue;  // did not fit
                     const bool timing = ctx->timing;
-                    if (!ctx->tev[0])
-                        for (auto& ev : ctx->tev) CU(cudaEventCreate(&ev));
+                    if (ensure_timing_events(ctx, 1)) continue;
                     ctx->timing = true;
-                    process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, epw, s);  // warm
-                    process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, epw, s);
+                    if (plan_waves(ctx, hits, epw, s)) continue;
+                    ctx->use_rec = false;  // this loop times the binning association
+                    process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s);  // warm
+                    process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s);
                     CU(cudaStreamSynchronize(s));
                     ctx->timing = timing;
                     float ms = 0;

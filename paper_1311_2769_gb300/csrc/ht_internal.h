@@ -30,6 +30,16 @@ struct VoteParams {
     const float4* edtab;   // range voting: the n_d0 + 1 d0 edges, as dtab
     KConsts K;
     unsigned long long* stats;
+    // vote records (band vote only; nullptr: none).  For every hit whose d0
+    // band meets a tile, the bins of the tile's cells, one byte each (255: no
+    // vote), `rec_bytes` = tile_phi * tile_d bytes per record, columns outer,
+    // phi rows inner; record of (wave event e, tile t, hit h) at
+    // ((hb - whb) * tiles + t * n_e + (h - hb)) * rec_bytes, whb the wave's
+    // first hit.  rbits: one bit per (tile, hit) marking the hits that have a
+    // record, words of event e from (((hb - whb) >> 5) + e) * tiles + t * ceil(n_e / 32).
+    uint8_t* rec;
+    uint32_t* rbits;
+    int32_t rec_bytes;
 };
 
 struct PeakParams {
@@ -84,6 +94,11 @@ struct AssocParams {
     const float4* dtab;
     KConsts K;
     unsigned long long* stats;
+    // association over vote records (items are the vote's tiles)
+    const uint8_t* rec;
+    const uint32_t* rbits;
+    int32_t rec_bytes;      // tile_phi * tile_d
+    int32_t rtiles_phi, rtiles_d, rtile_d;
 };
 
 // Exclusive scan of int32 counts over [lo, hi) (clamped to cap) into int64
@@ -103,7 +118,8 @@ struct ScanRange {
 constexpr int kScanBlocks = 304;
 constexpr int kScanThreads = 1024;
 
-// vote kernel variants: 0 full sweep, 1 d0-band compaction, 2 range voting
+// vote kernel variants: 0 full sweep, 1 d0-band compaction, 2 range voting,
+// 3 d0-band compaction writing vote records
 int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant);
 cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes, int variant);
 cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant);
@@ -129,6 +145,12 @@ size_t assoc_range_warp_smem(int wd, int nk, int cap);
 cudaError_t assoc_range_prepare(int nk, int smem, int threads, int* blocks_per_sm, bool line = false);
 cudaError_t launch_vote_line(const VoteParams& p, double d0min, double d0max, cudaStream_t s);
 cudaError_t launch_assoc_range(const AssocParams& p, bool count, int threads, int grid, cudaStream_t s);
+// association over vote records (ht_assoc_rec.cu): one warp per vote tile of
+// an event, lanes own the tile's cells
+bool assoc_rec_supported(int tile_phi, int tile_d, int nk);
+size_t assoc_rec_warp_smem(int tile_phi, int tile_d, int nk, int cap);
+cudaError_t assoc_rec_prepare(int tile_phi, int tile_d, int nk, int smem, int threads, int* blocks_per_sm);
+cudaError_t launch_assoc_rec(const AssocParams& p, int tile_phi, int threads, int grid, cudaStream_t s);
 // circle fit of the stored candidates' rows (ht_fit.cu)
 struct FitParams {
     const float* x;

@@ -58,6 +58,21 @@ __device__ __forceinline__ void red_if_vote(uint32_t addr, float flo, float fhi,
         "f"(flo), "f"(fhi), "r"(kb), "r"(nk), "r"((unsigned)valid));
 }
 
+// red_if_vote (TAIL form) that also sets byte `r` of a record word to the
+// certified bin, or 255 when the cell casts no certified vote (out of range,
+// undecided, or an idle lane): one predicate for both.
+__device__ __forceinline__ uint32_t red_and_byte(uint32_t addr, float flo, float fhi, unsigned kb, unsigned nk,
+                                                 bool valid, uint32_t word, unsigned pos) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b32 b;\n\tsetp.eq.f32 p, %2, %3;\n\tsetp.lt.and.u32 p, %4, %5, p;\n\t"
+        "setp.ne.and.u32 p, %6, 0, p;\n\t@p red.shared.add.u32 [%1], 1;\n\tselp.b32 b, %4, 255, p;\n\t"
+        "bfi.b32 %0, b, %7, %8, 8;\n\t}"
+        : "=r"(out)
+        : "r"(addr), "f"(flo), "f"(fhi), "r"(kb), "r"(nk), "r"((unsigned)valid), "r"(word), "r"(pos));
+    return out;
+}
+
 struct TileHit {
     float x, y;
     HitFast hf;
@@ -109,6 +124,72 @@ __device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* c
                 }
             }
         }
+    }
+}
+
+// Packed bins of one column's SPHI cells (one byte per phi row, row 0 in
+// the lowest byte; 255: no vote).
+template <int SPHI> struct RecWord { using T = uint32_t; };
+template <> struct RecWord<1> { using T = uint8_t; };
+template <> struct RecWord<2> { using T = uint16_t; };
+template <> struct RecWord<8> { using T = unsigned long long; };
+
+// vote_one_hit (TAIL form) that also writes the hit's record for the tile:
+// every column of [ja, jb] gets its rows' certified (or stage 2/3) bins, the
+// columns outside the warp's hull 255 (a hit votes nowhere outside its own
+// band, and the hull contains it).  `rec` is the lane's record (valid lanes).
+template <int SPHI, int NK>
+__device__ __forceinline__ void vote_one_hit_rec(const VoteParams& p, const float* cp, const float* sp,
+                                                 const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
+                                                 int nk, int64_t h, bool valid, uint8_t* rec) {
+    using W = typename RecWord<SPHI>::T;
+    const float x = valid ? p.x[h] : 0.0f;
+    const float y = valid ? p.y[h] : 0.0f;
+    const HitFast hf = hit_fast(x, y, p.K);
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    float q[SPHI], qs[SPHI];
+#pragma unroll
+    for (int r = 0; r < SPHI; ++r) {
+        q[r] = q_of(x, y, cp[r], sp[r]);
+        qs[r] = q[r] * S2;
+    }
+    const unsigned nku = (unsigned)nk;
+    const int col_words = SPHI * nk;
+    W* rw = reinterpret_cast<W*>(rec);
+    if (valid) {
+        const W none = (W)~(W)0;
+        for (int j = 0; j < ja; ++j) rw[j] = none;
+        for (int j = jb + 1; j < p.tile_d; ++j) rw[j] = none;
+    }
+    uint32_t col_sh = acc_sh + 4u * (unsigned)(ja * col_words);
+    for (int j = ja; j <= jb; ++j, col_sh += 4u * col_words) {
+        const float4 dt = dt_s[j];
+        const float Rj = hf.r2 + dt.z;
+        bool und = false;
+        uint32_t wlo = 0, whi = 0;  // rows 0-3 and 4-7
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+            const uint32_t addr = col_sh + 4u * ((unsigned)(r * nk) + o.kb);
+            if (r < 4)
+                wlo = red_and_byte(addr, o.flo, o.fhi, o.kb, nku, valid, wlo, 8u * r);
+            else
+                whi = red_and_byte(addr, o.flo, o.fhi, o.kb, nku, valid, whi, 8u * (r - 4));
+            und |= (o.flo != o.fhi) & valid;
+        }
+        W word = (W)(SPHI == 8 ? ((unsigned long long)whi << 32) | wlo : wlo);
+        if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+                if ((o.flo != o.fhi) && valid && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi)) {
+                    const int kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                    if (kk >= 0) atomicAdd(acc_s + j * col_words + r * nk + kk, 1u);
+                    word = (word & ~((W)0xFF << (8 * r))) | ((W)(kk >= 0 ? (unsigned)kk : 255u) << (8 * r));
+                }
+            }
+        }
+        if (valid) rw[j] = word;
     }
 }
 
@@ -206,20 +287,24 @@ __global__ void __launch_bounds__(256, 3) vote_kernel(const VoteParams p) {
 // of a 4 x 16 tile have an empty band.
 constexpr int kHitQueue = 64;  // per-warp queue of banded hits (run 32 at a time)
 
-template <int SPHI, int NK>
+template <int SPHI, int NK, bool REC>
 __device__ __forceinline__ void vote_queued(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
                                             uint32_t* acc_s, uint32_t acc_sh, const uint2* hq, unsigned head, int n,
-                                            int nj, int nk, int lane) {
+                                            int nj, int nk, int lane, uint8_t* rec_t, int64_t hb) {
     __syncwarp();
     const bool valid = lane < n;
     const uint2 ent = valid ? hq[(head + lane) & (kHitQueue - 1)] : make_uint2(0u, 0u);
     const int lo = valid ? (int)(ent.y & 0xFFFFu) : nj, hi = valid ? (int)(ent.y >> 16) : -1;
     const int ja = __reduce_min_sync(0xffffffffu, lo), jb = __reduce_max_sync(0xffffffffu, hi);
     __syncwarp();  // entries read before their slots are reused
-    vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid);
+    if (REC)
+        vote_one_hit_rec<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid,
+                                   rec_t + ((int64_t)ent.x - hb) * p.rec_bytes);
+    else
+        vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid);
 }
 
-template <int SPHI, int NK>
+template <int SPHI, int NK, bool REC>
 __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* dt_s = reinterpret_cast<float4*>(smem_raw);
@@ -271,6 +356,21 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
         __syncthreads();
 
         const float dlo = dt_s[0].x, dhi = dt_s[nj - 1].x;
+        // this tile's records and in-band bitmap words (REC)
+        uint8_t* rec_t = nullptr;
+        uint32_t* bits_t = nullptr;
+        if (REC) {
+            // within the wave's hits even for offsets the validation rejects
+            // (the records are sized for the wave)
+            const int64_t whb = clamp64(p.offs[p.event0], 0, p.n_hits);
+            const int64_t wend = clamp64(p.offs[p.event0 + p.n_events], whb, p.n_hits);
+            if (hb < whb || he > wend) {
+                __syncthreads();
+                continue;
+            }
+            rec_t = p.rec + ((hb - whb) * tiles + (int64_t)t * (he - hb)) * p.rec_bytes;
+            bits_t = p.rbits + (((hb - whb) >> 5) + e) * (int64_t)tiles + (int64_t)t * ((he - hb + 31) >> 5);
+        }
         unsigned head = 0, tail = 0;
         for (int64_t c0 = hb + warp * 32; c0 < he; c0 += nthr) {
             const int64_t h = c0 + lane;
@@ -290,14 +390,17 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
             }
             const bool keep = valid && hi >= lo;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (REC && lane == 0) bits_t[(c0 - hb) >> 5] = m;
             if (keep) hq[(tail + __popc(m & lt)) & (kHitQueue - 1)] = make_uint2((unsigned)h, (unsigned)lo | ((unsigned)hi << 16));
             tail += __popc(m);
             if (tail - head >= 32) {
-                vote_queued<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, 32, nj, nk, lane);
+                vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, 32, nj, nk, lane, rec_t, hb);
                 head += 32;
             }
         }
-        if (tail != head) vote_queued<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, (int)(tail - head), nj, nk, lane);
+        if (tail != head)
+            vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, (int)(tail - head), nj, nk, lane, rec_t,
+                                       hb);
         __syncthreads();
 
         uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
@@ -1495,7 +1598,7 @@ __global__ void rcp_check_kernel(uint32_t first_bits, uint32_t count, unsigned l
 // launchers
 // ---------------------------------------------------------------------------
 int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant) {
-    const int queues = variant == 1 ? (threads / 32) * kHitQueue * 8 : 0;
+    const int queues = variant == 1 || variant == 3 ? (threads / 32) * kHitQueue * 8 : 0;
     const int table = variant == 2 ? 16 * (tile_d + 1) : 16 * tile_d;
     return table + queues + 4 * tile_phi * tile_d * nk;
 }
@@ -1526,18 +1629,20 @@ static void* vote_fn() {
     return reinterpret_cast<void*>(vote_kernel<S, N>);
 }
 template <int S, int N>
-static void* vote_band_fn() {
-    return reinterpret_cast<void*>(vote_band_kernel<S, N>);
+static void* vote_band_fn(bool rec) {
+    return rec ? reinterpret_cast<void*>(vote_band_kernel<S, N, true>)
+               : reinterpret_cast<void*>(vote_band_kernel<S, N, false>);
 }
 
-static void* vote_band_instance(int tile_phi, int nk) {
-#define HT_VOTEB_NK(S)                             \
-    switch (nk) {                                  \
-        case 64: return vote_band_fn<S, 64>();     \
-        case 128: return vote_band_fn<S, 128>();   \
-        case 256: return vote_band_fn<S, 256>();   \
-        case 512: return vote_band_fn<S, 512>();   \
-        default: return vote_band_fn<S, 0>();      \
+// records hold one byte per bin: only grids with n_kappa <= 255 write them
+static void* vote_band_instance(int tile_phi, int nk, bool rec) {
+#define HT_VOTEB_NK(S)                                     \
+    switch (nk) {                                          \
+        case 64: return vote_band_fn<S, 64>(rec);          \
+        case 128: return vote_band_fn<S, 128>(rec);        \
+        case 256: return vote_band_fn<S, 256>(false);      \
+        case 512: return vote_band_fn<S, 512>(false);      \
+        default: return vote_band_fn<S, 0>(rec && nk <= 255); \
     }
     switch (tile_phi) {
         case 1: HT_VOTEB_NK(1)
@@ -1593,9 +1698,11 @@ static void* vote_instance(int tile_phi, int nk) {
     return nullptr;
 }
 
+// variant 3: the band vote writing records
 static void* vote_variant(int tile_phi, int nk, int variant) {
     return variant == 2 ? vote_range_instance(tile_phi, nk)
-                        : (variant == 1 ? vote_band_instance(tile_phi, nk) : vote_instance(tile_phi, nk));
+                        : (variant == 1 || variant == 3 ? vote_band_instance(tile_phi, nk, variant == 3)
+                                                        : vote_instance(tile_phi, nk));
 }
 
 cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant) {

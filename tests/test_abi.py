@@ -63,3 +63,12 @@ def test_argument_checks_of_the_extension_calls_need_no_gpu(lib):
     assert lib.ht_merge(None, None, None, 2, None, 0, ctypes.byref(n), None) == -1
     assert lib.ht_vertices(None, None, None, 1, None, 0, ctypes.byref(n), None) == -1
     assert lib.ht_check_rcp(0, 0, None) == -1
+
+
+def test_binding_option_numbers_match_the_header():
+    from paper_1311_2769_gb300 import ht
+    src = open(os.path.join(ROOT, "include", "ht.h")).read()
+    opts = dict(re.findall(r"#define (HT_OPT_[A-Z0-9_]+) (\d+)", src))
+    assert opts
+    for name, value in opts.items():
+        assert getattr(ht, name) == int(value), name
