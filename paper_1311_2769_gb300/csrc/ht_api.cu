@@ -55,7 +55,7 @@ struct GraphKey {
 
 constexpr int64_t kDefaultBudget = 40LL << 30;
 constexpr int64_t kDefaultRecBudget = 72LL << 30;
-constexpr size_t kRecWarpBudget = 12288;  // shared memory per warp of the record association
+constexpr size_t kRecWarpBudget = 9728;  // shared memory per warp of the record association
 
 }  // namespace
 

@@ -45,35 +45,36 @@ constexpr int kRecStep = 8;
 constexpr int kRecBlock = 1024;  // hits whose bitmap words are read at once (32 words, one per lane)
 
 struct RecWarp {
+    // cell tables, one row per cell in lane-major order (row tt * 32 + L holds
+    // cell L * CPL + tt), so the lanes' lookups fall in different banks
     uint32_t* mask;   // [cells][nkw] peak bits of the tile's cells (0 outside the grid)
     int32_t* lpre;    // [cells][nkw] item-local id of the first peak of each word
     uint32_t* nearb;  // [cells][nkn] bins within `window` of a peak; bin nk (no bin) is 0
     long long* cur;   // [cap] row cursors (absolute positions) of the pass's peaks
-    uint32_t* qh;     // [kRecQueue][32] event-local hit index
-    uint32_t* qc;     // [kRecQueue][32] (cell in lane << 8) | bin
+    uint32_t* q;      // [kRecQueue][32] (cell in lane << 18) | (bin << 10) | hit offset in the block
     uint16_t* list;   // [kRecBlock] recorded hits of the current block (offsets in the block)
 };
 
 __host__ __device__ inline size_t rec_warp_bytes(int cells, int nk, int cap) {
     const size_t nkw = (nk + 31) / 32, nkn = nk / 32 + 1;
-    return (4 * (size_t)cells * (2 * nkw + nkn) + 8 * (size_t)cap + 8 * (size_t)kRecQueue * 32 +
+    return (4 * (size_t)cells * (2 * nkw + nkn) + 8 * (size_t)cap + 4 * (size_t)kRecQueue * 32 +
             2 * (size_t)kRecBlock + 15) &
            ~size_t(15);
 }
 
-// Write the queued candidates of every lane (each lane its own, in order).
+// Write the queued candidates of every lane (each lane its own, in order);
+// hbase is the first hit of the block the entries belong to.
 template <int CPL>
 __device__ __forceinline__ void rec_flush(const AssocParams& p, const RecWarp& S, int nkw, int nk, int qn, int L0,
-                                          int L1, int64_t hb, int lane) {
+                                          int L1, int64_t hbase, int lane) {
     const int mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)qn);
     const int w = p.window;
     for (int s = 0; s < mx; ++s) {
         if (s < qn) {
-            const uint32_t hl = S.qh[s * 32 + lane];
-            const uint32_t code = S.qc[s * 32 + lane];
-            const int c = lane * CPL + (int)(code >> 8);
-            const int b = (int)(code & 0xFFu);
-            const uint32_t* m = S.mask + c * nkw;
+            const uint32_t ent = S.q[s * 32 + lane];
+            const int row = (int)(ent >> 18) * 32 + lane;
+            const int b = (int)((ent >> 10) & 0xFFu);
+            const uint32_t* m = S.mask + row * nkw;
             const int lo = max(b - w, 0), hi = min(b + w, nk - 1);
             const int a = lo >> 5, bw = hi >> 5;  // bw <= a + 1 since 2w < 32
             const unsigned long long two =
@@ -82,16 +83,31 @@ __device__ __forceinline__ void rec_flush(const AssocParams& p, const RecWarp& S
             for (; pend; pend &= pend - 1u) {
                 const int kk = lo + __ffs(pend) - 1;
                 const uint32_t word = m[kk >> 5];
-                const int local = S.lpre[c * nkw + (kk >> 5)] + __popc(word & ((1u << (kk & 31)) - 1u));
+                const int local = S.lpre[row * nkw + (kk >> 5)] + __popc(word & ((1u << (kk & 31)) - 1u));
                 if (local >= L0 && local < L1) {
                     const long long pos = S.cur[local - L0];
                     S.cur[local - L0] = pos + 1;
-                    if (pos < p.pair_cap) p.hit_idx[pos] = (int32_t)(hb + (int64_t)hl);
+                    if (pos < p.pair_cap) p.hit_idx[pos] = (int32_t)(hbase + (int64_t)(ent & 0x3FFu));
                 }
             }
         }
     }
     __syncwarp();
+}
+
+// Test CPL cells of one recorded hit (`off` in its block) and queue the near ones.
+template <int CPL, typename LT>
+__device__ __forceinline__ void rec_test(const RecWarp& S, LT v, uint32_t off, int nk, int nkn, int lane, int& qn) {
+#pragma unroll
+    for (int tt = 0; tt < CPL; ++tt) {
+        const unsigned b = (unsigned)(v >> (8 * tt)) & 0xFFu;
+        const unsigned bb = min(b, (unsigned)nk);
+        const int row = tt * 32 + lane;
+        if ((S.nearb[row * nkn + (bb >> 5)] >> (bb & 31)) & 1u) {
+            S.q[qn * 32 + lane] = ((unsigned)tt << 18) | (b << 10) | off;
+            ++qn;
+        }
+    }
 }
 
 template <int SPHI, int CPL>
@@ -101,7 +117,7 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
     constexpr int CELLS = 32 * CPL;
     constexpr int TD = CELLS / SPHI;  // record columns (the vote tile's d0 width)
     constexpr int U = kRecStep;
-    constexpr int kRecCheck = 8 / CPL;  // hits between queue checks
+    constexpr int kRecCheck = 8 / CPL;  // hits between queue checks (<= 8 new entries per lane)
     const int nk = p.K.nk;
     const int nkw = (nk + 31) >> 5;
     const int nkn = (nk >> 5) + 1;
@@ -111,9 +127,7 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
         unsigned char* ptr = smem_raw + (size_t)warp * p.warp_bytes;
         S.cur = reinterpret_cast<long long*>(ptr);
         ptr += 8 * (size_t)p.cap;
-        S.qh = reinterpret_cast<uint32_t*>(ptr);
-        ptr += 4 * kRecQueue * 32;
-        S.qc = reinterpret_cast<uint32_t*>(ptr);
+        S.q = reinterpret_cast<uint32_t*>(ptr);
         ptr += 4 * kRecQueue * 32;
         S.list = reinterpret_cast<uint16_t*>(ptr);
         ptr += 2 * kRecBlock;
@@ -165,7 +179,8 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
         if (hb < whb || he > wend) continue;  // offsets the validation rejects: no records were written
         __syncwarp();  // the previous item's tables are no longer read
         for (int v = lane; v < CELLS * nkw; v += 32) {
-            const int c = v / nkw, wd = v - (v / nkw) * nkw;
+            const int row = v / nkw, wd = v - (v / nkw) * nkw;
+            const int c = (row & 31) * CPL + (row >> 5);
             const int j = c / SPHI, r = c - (c / SPHI) * SPHI;
             const bool ok = r < nrows && j < nj;
             const int64_t col = ((int64_t)e * p.K.nphi + i0 + r) * p.K.nd + j0 + j;
@@ -176,8 +191,8 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
         }
         __syncwarp();
         for (int v = lane; v < CELLS * nkn; v += 32) {
-            const int c = v / nkn, wd = v - (v / nkn) * nkn;
-            const uint32_t* m = S.mask + c * nkw;
+            const int row = v / nkn, wd = v - (v / nkn) * nkn;
+            const uint32_t* m = S.mask + row * nkw;
             const uint32_t mw = wd < nkw ? m[wd] : 0u;
             const uint32_t hi_w = wd + 1 < nkw ? m[wd + 1] : 0u, lo_w = wd > 0 && wd - 1 < nkw ? m[wd - 1] : 0u;
             uint32_t nb = mw;
@@ -201,7 +216,6 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
                 S.cur[l - L0] = g < p.peak_cap ? (long long)p.peak_offsets[g] : LLONG_MAX / 2;
             }
             __syncwarp();
-            int qn = 0;
             for (int cw0 = 0; cw0 < nwords; cw0 += 32) {
                 // the block's recorded hits, in order, as offsets from its first hit
                 const uint32_t myw = cw0 + lane < nwords ? bits_t[cw0 + lane] : 0u;
@@ -218,51 +232,39 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
                 for (unsigned b = myw; b; b &= b - 1u) S.list[pre++] = (uint16_t)(lane * 32 + __ffs(b) - 1);
                 __syncwarp();
                 const uint8_t* blk = recb + (int64_t)cw0 * 32 * p.rec_bytes;
-                // step s tests hits list[s*U .. s*U+U) while the loads of step s + 1 are in flight
-                uint32_t hn[U];
-                LT vn[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const bool hv = u < n;
-                    hn[u] = hv ? S.list[u] : 0u;
-                    vn[u] = hv ? *reinterpret_cast<const LT*>(blk + (int64_t)hn[u] * p.rec_bytes) : (LT)~(LT)0;
-                }
-                for (int s0 = 0; s0 < n; s0 += U) {
-                    uint32_t hl[U];
-                    LT v[U];
+                // two buffers of U hits: the loads of one are in flight while
+                // the other's records are tested
+                uint32_t ha[U], hb2[U];
+                LT va[U], vb[U];
+                auto load = [&](uint32_t* hh, LT* vv, int first) {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        hl[u] = hn[u];
-                        v[u] = vn[u];
+                        const bool hv = first + u < n;
+                        hh[u] = hv ? S.list[first + u] : 0u;
+                        vv[u] = hv ? *reinterpret_cast<const LT*>(blk + (int64_t)hh[u] * p.rec_bytes) : (LT)~(LT)0;
                     }
+                };
+                int qn = 0;
+                auto test = [&](const uint32_t* hh, const LT* vv) {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const bool hv = s0 + U + u < n;
-                        hn[u] = hv ? S.list[s0 + U + u] : 0u;
-                        vn[u] = hv ? *reinterpret_cast<const LT*>(blk + (int64_t)hn[u] * p.rec_bytes) : (LT)~(LT)0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-#pragma unroll
-                        for (int tt = 0; tt < CPL; ++tt) {
-                            const unsigned b = (unsigned)(v[u] >> (8 * tt)) & 0xFFu;
-                            const unsigned bb = min(b, (unsigned)nk);
-                            const int c = lane * CPL + tt;
-                            if ((S.nearb[c * nkn + (bb >> 5)] >> (bb & 31)) & 1u) {
-                                S.qh[qn * 32 + lane] = (uint32_t)cw0 * 32u + hl[u];
-                                S.qc[qn * 32 + lane] = ((unsigned)tt << 8) | b;
-                                ++qn;
-                            }
-                        }
-                        // every kRecCheck hits (at most kRecCheck * CPL <= 8 new entries per lane)
+                        rec_test<CPL>(S, vv[u], hh[u], nk, nkn, lane, qn);
                         if ((u + 1) % kRecCheck == 0 && __any_sync(0xffffffffu, qn > kRecQueue - 8)) {
-                            rec_flush<CPL>(p, S, nkw, nk, qn, L0, L1, hb, lane);
+                            rec_flush<CPL>(p, S, nkw, nk, qn, L0, L1, hb + (int64_t)cw0 * 32, lane);
                             qn = 0;
                         }
                     }
+                };
+                load(ha, va, 0);
+                for (int s0 = 0; s0 < n; s0 += 2 * U) {
+                    load(hb2, vb, s0 + U);
+                    test(ha, va);
+                    if (s0 + U >= n) break;
+                    load(ha, va, s0 + 2 * U);
+                    test(hb2, vb);
                 }
+                rec_flush<CPL>(p, S, nkw, nk, qn, L0, L1, hb + (int64_t)cw0 * 32, lane);
             }
-            rec_flush<CPL>(p, S, nkw, nk, qn, L0, L1, hb, lane);
         }
     }
 }
