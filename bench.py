@@ -3,13 +3,14 @@
 
 One step = vote + peaks + association of one batch of 4096 ragged synthetic
 trigger events (tracks/event lognormal, median 150; 256 x 32 x 128 grid;
-threshold 9, window 1), run as one persistent launch per kernel replayed from
-a CUDA graph.  Inputs are resident in HBM when the timed region starts;
-the L2 is flushed between timed steps.  Also reported: the plain
-one-event-per-launch form on a sample of the same batch, the end-to-end
-rate through the C ABI with pinned host buffers (copies inside the timed
-region), the vote kernel against its issue-rate roofline, and the CPU oracle
-on the host cores.
+threshold 9, window 1), run as one persistent launch per kernel and wave,
+replayed from a CUDA graph.  Inputs are resident in HBM when the timed region
+starts; the L2 is flushed between timed steps.  Also reported: the plain
+one-event-per-launch form on a sample of the same batch, the end-to-end rate
+through the C ABI with pinned host buffers (copies inside the timed region),
+the dense single event and the pileup batch, the dominant kernels against
+their rooflines, the flip fraction of a plain float32 evaluation, and the CPU
+oracle on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 Under torchrun each rank processes its own batch (weak scaling, no collective).
@@ -35,12 +36,19 @@ WORKLOAD = "batch_4096_lognormal"
 METRIC = "events/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one launch on the 512-event case of the batch
-# workload, from ncu (profiles/assoc_kernel_batch512.md: 1.2365 + 2.3600 GB;
-# profiles/vote_band_kernel_batch512.md: 0.0197 + 2.0874 GB); set to None when
-# the kernel changes until it is captured again
-ASSOC_DRAM_512 = (1.236538 + 2.360003) * 1e9
-VOTE_DRAM_512 = (0.019719 + 2.087443) * 1e9
+# DRAM bytes (read + write) per hit of one launch on the first 64 events of
+# the batch workload (275,323 hits), from one ncu capture of the kernels as
+# they are now (vote_band_kernel<4, 128, 1> writing records: 0.163314 GB read
+# + 1.321358 GB written; assoc_rec_kernel<4, 2>: 1.713009 + 0.389908 GB); set
+# to None when a kernel changes until it is captured again
+PROFILE_HITS = 275323
+VOTE_DRAM_PER_HIT = (0.163314 + 1.321358) * 1e9 / PROFILE_HITS
+ASSOC_DRAM_PER_HIT = (1.713009 + 0.389908) * 1e9 / PROFILE_HITS
+# FP32 lane operations per (hit, phi0, d0) cell of the method: 8 arithmetic
+# (q: 2 products and a difference; a = q - d; den: d^2 and 2dq terms, 3; the
+# kappa scale) + 1 IEEE division + 4 compare/convert (den > 0, w >= 0,
+# w < n_kappa, the floor)
+OPS_PER_CELL = 13
 
 
 def _dist():
@@ -134,37 +142,104 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(w, batch, budget_s=15.0, max_events=None):
-    """The oracle as it stands, event-parallel on every host core, on a bounded
-    prefix of the workload's events (sized to about budget_s seconds)."""
+def cpu_single_thread_worker():
+    """--cpu-single-thread: the oracle on one host thread, on the whole
+    single event, the whole dense event and an 8-event subset of the batch
+    (extrapolated per event), plus the flip fraction of the plain float32
+    evaluation against the binary64 bins on a sample of every workload.
+    Prints one JSON line.  Started by the CPU-baseline leg as its own process
+    before any GPU work, so it runs while the GPU is timed."""
+    import oracle
+    from paper_1311_2769_gb300 import synth
+    oracle.build()
+    out = {"threads": 1, "events": {}, "flip_fraction_plain_fp32": {}}
+    for name, n in (("single_event_10trk", 1), ("batch_4096_lognormal", 8), ("dense_event_500trk", 1)):
+        w = synth.WORKLOADS[name]
+        b = synth.generate(w, n_events=n)
+        t0 = time.perf_counter()
+        votes, peaks, pairs = oracle.run_events(w.grid, b.x, b.y, b.event_offsets, w.threshold, w.window, 1)
+        dt = time.perf_counter() - t0
+        row = {"events": n, "hits": int(b.n_hits), "seconds": dt, "events_per_s": n / dt,
+               "hit_votes_per_s": float(b.n_hits) * w.grid.n_phi * w.grid.n_d0 / dt,
+               "votes": votes, "peaks": peaks, "pairs": pairs}
+        if n > 1:
+            row["note"] = f"events 0..{n - 1} of the 4096-event batch; per-event rate extrapolated to the batch"
+        out["events"][name] = row
+    # plain float32 op order (no contraction) against the binary64 bins
+    for name, n_hits in (("single_event_10trk", None), ("dense_event_500trk", 300), ("batch_4096_lognormal", None),
+                         ("pileup_64x5000trk", 300)):
+        w = synth.WORKLOADS[name]
+        b = synth.generate(w, n_events=1)
+        x, y = b.x, b.y
+        if n_hits and len(x) > n_hits:
+            sel = np.random.default_rng(1).choice(len(x), n_hits, replace=False)
+            x, y = x[sel], y[sel]
+        v64, v32, diff = oracle.flip_count(w.grid, x, y)
+        out["flip_fraction_plain_fp32"][name] = {"binary64_votes": v64, "columns_differing": diff,
+                                                 "fraction": diff / max(v64, 1), "hits": int(len(x)),
+                                                 "sample": "event 0" + (f", {n_hits} random hits" if n_hits else "")}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_single_thread_start():
+    """Start the single-thread oracle worker (a fresh process, before the
+    first GPU call)."""
+    try:
+        return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-single-thread"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, cwd=ROOT)
+    except OSError:
+        return None
+
+
+def cpu_single_thread_finish(proc, timeout=300):
+    if proc is None:
+        return {"error": "not started"}
+    try:
+        out, _ = proc.communicate(timeout=timeout)
+        return json.loads(out.strip().splitlines()[-1])
+    except Exception as e:  # report, do not hide, a failing worker
+        proc.kill()
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def cpu_baseline(w, batch, budget_s=15.0, single=None):
+    """The oracle as it stands, event-parallel on every host core (largest
+    event first, one event at a time per thread), on a prefix of the
+    workload's events whose length is a multiple of the core count and at
+    least four events per core (sized to about budget_s seconds)."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    # calibrate on one small batch, then size the sample
+    # calibrate on one event per core, then size the sample
     n = min(cores, batch.n_events)
     sub = batch.select(range(n))
     t0 = time.perf_counter()
     oracle.run_events(w.grid, sub.x, sub.y, sub.event_offsets, w.threshold, w.window, cores)
     dt = time.perf_counter() - t0
     per_event = dt * cores / n
-    want = int(max(n, min(batch.n_events, budget_s * cores / max(per_event, 1e-9))))
-    if max_events:
-        want = min(want, max_events)
+    want = int(budget_s * cores / max(per_event, 1e-9))
+    want = max(4 * cores, (want // cores) * cores)
+    want = min(want, batch.n_events)
     sub = batch.select(range(want))
     t0 = time.perf_counter()
     votes, peaks, pairs = oracle.run_events(w.grid, sub.x, sub.y, sub.event_offsets, w.threshold, w.window, cores)
     dt = time.perf_counter() - t0
-    return {"value": want / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"events 0..{want - 1} of the 4096-event batch ({sub.n_hits} hits), "
-                      f"vote+peaks+association, one event per thread", "seconds": dt,
-            "hit_votes_per_s": float(sub.n_hits) * w.grid.n_phi * w.grid.n_d0 / dt}
+    out = {"value": want / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"events 0..{want - 1} of the 4096-event batch ({sub.n_hits} hits), "
+                     f"vote+peaks+association, one event per thread, largest first", "seconds": dt,
+           "hit_votes_per_s": float(sub.n_hits) * w.grid.n_phi * w.grid.n_d0 / dt,
+           "all_cores": {"threads": cores, "events": want, "events_per_s": want / dt}}
+    if single is not None:
+        out["single_thread"] = single
+    return out
 
 
 def vote_ceilings(ht, g, batch, w, cells, vote_s, vote_traffic, peaks, dev, sample_events=64):
     """The vote kernel against each ceiling it could meet, every ceiling
-    measured here: FP32 issue (6 lane operations per cell), IEEE division
-    (one per cell), shared-memory increments (one per accepted vote; the
-    accepted fraction of cells is counted on the first `sample_events`
+    measured here: FP32 issue (OPS_PER_CELL lane operations per cell), IEEE
+    division (one per cell), shared-memory increments (one per accepted vote;
+    the accepted fraction of cells is counted on the first `sample_events`
     events) and HBM (its ncu DRAM traffic).  `binding` names the largest
     fraction."""
     rates = {"fp32_ops_per_s": ht.ht_microbench(ht.HT_MB_FP32, 160000),
@@ -176,7 +251,7 @@ def vote_ceilings(ht, g, batch, w, cells, vote_s, vote_traffic, peaks, dev, samp
     votes = sum(int(c2.accumulator(e).sum(dtype=np.int64)) for e in range(sub.n_events))
     c2.close()
     accepted = votes / (float(sub.n_hits) * g.n_phi * g.n_d0)
-    frac = {"issue": 6.0 * cells / vote_s / rates["fp32_ops_per_s"],
+    frac = {"issue": float(OPS_PER_CELL) * cells / vote_s / rates["fp32_ops_per_s"],
             "shared_atomic": accepted * cells / vote_s / rates["shared_red_per_s"]}
     if vote_traffic and peaks.get("hbm_gbs"):
         frac["hbm"] = vote_traffic / vote_s / (peaks["hbm_gbs"] * 1e9)
@@ -337,7 +412,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    n_sample = max(cores, 2 * cores)
+    n_sample = 4 * cores  # four events per core, handed out largest first
     batch = synth.generate(w, n_events=n_sample)
     for _ in range(args.warmup):
         sub = batch.select(range(min(cores, n_sample)))
@@ -347,7 +422,7 @@ def run_reference(args):
         t0 = time.perf_counter()
         oracle.run_events(w.grid, batch.x, batch.y, batch.event_offsets, w.threshold, w.window, cores)
         times.append(time.perf_counter() - t0)
-    ms = 1e3 * float(np.mean(times))
+    ms = 1e3 * float(np.median(times))
     value = n_sample / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -355,19 +430,76 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "events_per_step": n_sample, "grid": [256, 32, 128],
                        "threshold": w.threshold, "window": w.window},
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": METRIC,
-                             "sample": f"events 0..{n_sample - 1} of the 4096-event batch per step"},
+                             "sample": f"events 0..{n_sample - 1} of the 4096-event batch per step, "
+                                       f"one event at a time per thread, largest first"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _median_ms(fn, stream, flush, reps):
+    """Median device time (CUDA events on `stream`) of `fn` over reps calls,
+    the L2 flushed before each."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms)), ms
+
+
+def secondary_workloads(dev, stream, flush, reps=5):
+    """The dense single event (8.5k hits, 512 x 64 x 256 grid) and the pileup
+    batch (64 events of ~76k hits, 1024 x 128 x 512 grid, accumulators
+    admitted four events at a time), each timed as whole steps on the device
+    (median of `reps`, 3 for pileup, L2 flushed before each)."""
+    from paper_1311_2769_gb300 import ht, synth
+    out = {}
+    for name, waves_of, r in (("dense_event_500trk", 0, reps), ("pileup_64x5000trk", 4, 3)):
+        w = synth.WORKLOADS[name]
+        g = w.grid
+        b = synth.generate(w)
+        ctx = ht.Context(g, w.spec.layers)
+        if waves_of:
+            ctx.set_option(ht.HT_OPT_ACC_BUDGET, waves_of * 4 * g.n_phi * g.n_d0 * g.n_kappa)
+        hits = ht.Hits.from_batch(b, device=dev)
+        probe = ht.Results(1 << 20, 1 << 20, device=dev)
+        ctx.process(hits, w.threshold, w.window, probe, stream)
+        ctx.sync(allow_overflow=True)
+        n_peaks, n_pairs = (int(v) for v in probe.counts.cpu().numpy())
+        del probe
+        res = ht.Results(n_peaks + 1024, n_pairs + 4096, device=dev)
+        step = lambda: ctx.process(hits, w.threshold, w.window, res, stream)
+        step()
+        ctx.sync()
+        med, all_ms = _median_ms(step, stream, flush, r)
+        out[name] = {"events": b.n_events, "hits": int(b.n_hits), "grid": [g.n_phi, g.n_d0, g.n_kappa],
+                     "threshold": w.threshold, "ms_per_step": med, "events_per_s": b.n_events / (med / 1e3),
+                     "hit_votes_per_s": float(b.n_hits) * g.n_phi * g.n_d0 / (med / 1e3),
+                     "peaks": n_peaks, "pairs": n_pairs, "waves": ctx.get_option(ht.HT_OPT_WAVES),
+                     "records": ctx.get_option(ht.HT_OPT_RECORDS), "runs_ms": all_ms}
+        ctx.close()
+        del res, hits
+    return out
 
 
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
+    rank, world, local = _dist()
+    single_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
+        single_proc = cpu_single_thread_start()  # its own process, before the first GPU call
+
     from paper_1311_2769_gb300 import build, ht, synth
 
-    rank, world, local = _dist()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -385,6 +517,8 @@ def run_gpu(args):
     if args.waves_of:
         # accumulator memory admitted for this many events at a time (waves)
         ctx.set_option(ht.HT_OPT_ACC_BUDGET, args.waves_of * 4 * g.n_phi * g.n_d0 * g.n_kappa)
+    if args.record_budget_gb:
+        ctx.set_option(ht.HT_OPT_RECORD_BUDGET, int(args.record_budget_gb * 2 ** 30))
     hits_d = ht.Hits.from_batch(batch, device=dev)
     if args.prune is not None:
         ctx.set_option(ht.HT_OPT_PRUNE, args.prune)
@@ -392,11 +526,16 @@ def run_gpu(args):
         for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
             ctx.set_option(k, int(v))
     else:
-        # autotune the vote tile on a sample of the batch (outside the timed region)
+        # autotune the tile on the batch itself (outside the timed region):
+        # timings on a smaller sample ranked the tiles differently from the
+        # full step
         per_ev = 4 * g.n_phi * g.n_d0 * g.n_kappa
-        n_s = max(1, min(256, n_events, ctx.get_option(ht.HT_OPT_ACC_BUDGET) // per_ev))
-        sample = batch.select(range(0, n_events, max(1, n_events // n_s))[:n_s])
-        ctx.autotune(ht.Hits.from_batch(sample, device=dev))
+        n_s = max(1, min(n_events, ctx.get_option(ht.HT_OPT_ACC_BUDGET) // per_ev))
+        if n_s == n_events:
+            ctx.autotune(hits_d)
+        else:
+            sample = batch.select(range(0, n_events, max(1, n_events // n_s))[:n_s])
+            ctx.autotune(ht.Hits.from_batch(sample, device=dev))
     tile = {"tile_phi": ctx.get_option(ht.HT_OPT_TILE_PHI), "tile_d0": ctx.get_option(ht.HT_OPT_TILE_D0),
             "threads": ctx.get_option(ht.HT_OPT_THREADS)}
 
@@ -444,9 +583,11 @@ def run_gpu(args):
         dist.barrier()
     ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
     launches = ctx.get_option(ht.HT_OPT_LAUNCHES)
+    waves = ctx.get_option(ht.HT_OPT_WAVES)
     counts = res.counts.cpu().numpy()
     # ---- end to end through the C ABI: pinned host inputs and outputs (measured
-    # right after the device steps, before the reports below allocate)
+    # right after the device steps, before the reports below allocate); the
+    # same context, so the batch's record memory is held once
     e2e = None
     if not args.no_extras:  # every rank measures its own end-to-end rate
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -463,20 +604,15 @@ def run_gpu(args):
         rh.counts = torch.zeros(2, dtype=torch.int64).pin_memory()
         rh.struct = ht.HtResults(rh.peaks.data_ptr(), rh.peak_cap, rh.peak_offsets.data_ptr(),
                                  rh.hit_idx.data_ptr(), rh.pair_cap, rh.counts.data_ptr(), ht.HT_HOST)
-        ectx = ht.Context(g, w.spec.layers)
-        for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
-                     (ht.HT_OPT_THREADS, tile["threads"])):
-            ectx.set_option(k, v)
-        for _ in range(2):  # warm: graph capture, buffers, first DMA into the pinned pages
-            ectx.process(hits_h, w.threshold, w.window, rh, stream)
+        for _ in range(2):  # warm: buffers, first DMA into the pinned pages
+            ctx.process(hits_h, w.threshold, w.window, rh, stream)
         et = []
-        for _ in range(max(1, min(args.steps, 3))):
+        for _ in range(max(5, min(args.steps, 9))):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ectx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
+            ctx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
             et.append(time.perf_counter() - t0)
-        ectx.close()
         c = rh.counts.numpy()
         h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
         d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
@@ -489,10 +625,15 @@ def run_gpu(args):
         rh.hit_idx[:n_copy].copy_(res.hit_idx[:n_copy], non_blocking=True)
         d1.record(stream)
         d1.synchronize()
-        e2e_s = max_over_ranks(float(np.mean(et)), world, dev)
+        e2e_s = max_over_ranks(float(np.median(et)), world, dev)
         e2e = {"value": world * n_events / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s, "runs_s": et, "stat": "median",
+               "waves": ctx.get_option(ht.HT_OPT_WAVES),
                "d2h_gbs": 4.0 * n_copy / (d0.elapsed_time(d1) * 1e-3) / 1e9}
+        del rh, hits_h
+        # the device results again for the reports below
+        step()
+        ctx.sync()
 
     # circle fit of the stored candidates of the last step (not in the step)
     fit_ms = []
@@ -531,19 +672,26 @@ def run_gpu(args):
                   "duplicate": int(st[2]), "backward": int(st[1]), "unfitted": int(st[0]),
                   "candidates_per_s": n_fit / (float(np.median(merge_ms)) / 1e3)}
     del fits, state
+    records = ctx.get_option(ht.HT_OPT_RECORDS)
+    prune = ctx.get_option(ht.HT_OPT_PRUNE)
+    # the step's context holds the batch's records and accumulators: free it
+    # before the reports below allocate their own
+    ctx.close()
+    del res, hits_d
+    torch.cuda.empty_cache()
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_events / (ms / 1e3), "ms_per_step": ms,
                               "workload": args.workload, "hit_votes_per_s": world * hit_votes / (ms / 1e3),
-                              "prune": ctx.get_option(ht.HT_OPT_PRUNE),
+                              "prune": prune, "waves": waves, "records": records,
                               "events": n_events, "phase_ms": {"vote": float(np.mean(vote_ms)),
                                                                "peaks_assoc": float(np.mean(rest_ms)),
                                                                "assoc": float(np.mean(assoc_ms))},
                               "peaks": int(counts[0]), "pairs": int(counts[1]), "tile": tile}), flush=True)
-        ctx.close()
         return 0
 
-    # ---- plain form (one launch sequence per event) on a 512-event sample
+    # ---- plain form (one launch sequence per event) on a 512-event sample,
+    # median of five timed runs
     plain_ctx = ht.Context(g, w.spec.layers)
     for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
                  (ht.HT_OPT_THREADS, tile["threads"]), (ht.HT_OPT_MODE, ht.HT_MODE_PLAIN)):
@@ -553,22 +701,22 @@ def run_gpu(args):
     pres = ht.Results(int(n_peaks * 0.2) + 4096, int(n_pairs * 0.2) + 65536, device=dev)
     plain_ctx.process(ph, w.threshold, w.window, pres, stream)
     plain_ctx.sync(allow_overflow=True)
-    p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
-    flush.fill_(1.0)
-    p0.record(stream)
-    plain_ctx.process(ph, w.threshold, w.window, pres, stream)
-    p1.record(stream)
-    plain_ctx.sync(allow_overflow=True)
-    plain_eps = psub.n_events / (p0.elapsed_time(p1) / 1e3)
-    plain_ctx.close()
 
-    # ---- serving: continuous batching at two offered loads (rank 0, N=1)
+    def plain_step():
+        plain_ctx.process(ph, w.threshold, w.window, pres, stream)
+
+    plain_ms, plain_runs = _median_ms(plain_step, stream, flush, 5)
+    plain_ctx.sync(allow_overflow=True)
+    plain_eps = psub.n_events / (plain_ms / 1e3)
+    plain_ctx.close()
+    del pres, ph
+
+    # ---- serving: continuous batching at offered loads below and above capacity (rank 0, N=1)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         from paper_1311_2769_gb300 import serve
         try:
-            serving = serve.measure([50000.0, 200000.0], n_events=3000)
+            serving = serve.measure([2000.0, 5000.0, 10000.0, 13000.0, 20000.0, 50000.0], n_events=2000)
         except Exception as e:  # report, do not hide, a failing loop
             serving = {"error": f"{type(e).__name__}: {e}"}
 
@@ -588,28 +736,61 @@ def run_gpu(args):
         except Exception as e:
             vertex = {"error": f"{type(e).__name__}: {e}"}
 
-    # ---- roofline of the dominant kernel (association) and of the vote:
-    # issue-bound ALU work, 6 ops per (hit, phi0, d0) cell of the method
+    # ---- the dense event and the pileup batch (rank 0, N=1)
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        try:
+            secondary = secondary_workloads(dev, stream, flush)
+        except Exception as e:
+            secondary = {"error": f"{type(e).__name__}: {e}"}
+
+    # ---- rooflines of the two hot kernels: the method's FP32 work per
+    # (hit, phi0, d0) cell (OPS_PER_CELL) against 152 SMs x 128 lanes x the
+    # sampled clock; the dominant one (longer device time per step) is `roofline`
     peaks, peak_src = _peaks()
     clk = clocks.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     vote_s = float(np.mean(vote_ms)) / 1e3
     assoc_s = float(np.mean(assoc_ms)) / 1e3
-    ops_per_cell = 6  # add, fma, reciprocal, multiply, fma, bin test: the formula's minimum per cell
-    cells_per_launch = hit_votes
-    achieved = ops_per_cell * cells_per_launch / assoc_s / 1e12
-    achieved_vote = ops_per_cell * cells_per_launch / vote_s / 1e12
     peak_tops = sms * 128 * sm_mhz * 1e6 / 1e12
-    # DRAM read + write per launch from ncu on the 512-event case of this
-    # workload (profiles/*_batch512.md), scaled to a full launch by the hits
-    # processed; None where the kernel changed after the capture
-    hits512 = 2108472
-    assoc_traffic = ASSOC_DRAM_512 * n_hits / hits512 if ASSOC_DRAM_512 else None
-    vote_traffic = VOTE_DRAM_512 * n_hits / hits512 if VOTE_DRAM_512 else None
-    peak_basis = f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"
-    ceilings = vote_ceilings(ht, g, batch, w, hit_votes, vote_s, vote_traffic, peaks, dev) if rank == 0 else None
+    peak_basis = (f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock under load); "
+                  f"{OPS_PER_CELL} FP32 lane operations per (hit, phi0, d0) cell of the method: 8 arithmetic, "
+                  f"1 IEEE division, 4 compare/convert")
+    launches_per = max(1, waves)  # one launch of each kernel per wave
+    per_launch_cells = hit_votes / launches_per
+    vote_traffic = VOTE_DRAM_PER_HIT * n_hits / launches_per if VOTE_DRAM_PER_HIT else None
+    assoc_traffic = ASSOC_DRAM_PER_HIT * n_hits / launches_per if ASSOC_DRAM_PER_HIT else None
+    roof = {
+        "vote_band_kernel": {"bound": "alu", "achieved": OPS_PER_CELL * hit_votes / vote_s / 1e12, "peak": peak_tops,
+                             "unit": "TFLOP/s", "frac": OPS_PER_CELL * hit_votes / vote_s / 1e12 / peak_tops,
+                             "traffic": vote_traffic, "kernel": "vote_band_kernel", "ops_per_cell": OPS_PER_CELL,
+                             "cells_per_launch": per_launch_cells, "launches_per_step": launches_per,
+                             "ms_per_launch": 1e3 * vote_s / launches_per, "peak_basis": peak_basis},
+        "assoc_rec_kernel" if records else "assoc_kernel": {
+            "bound": "alu", "achieved": OPS_PER_CELL * hit_votes / assoc_s / 1e12, "peak": peak_tops,
+            "unit": "TFLOP/s", "frac": OPS_PER_CELL * hit_votes / assoc_s / 1e12 / peak_tops, "traffic": assoc_traffic,
+            "kernel": "assoc_rec_kernel" if records else "assoc_kernel", "ops_per_cell": OPS_PER_CELL,
+            "cells_per_launch": per_launch_cells, "launches_per_step": launches_per,
+            "ms_per_launch": 1e3 * assoc_s / launches_per,
+            "peak_basis": peak_basis + ("; the kernel decides every cell's association from the bins the vote "
+                                        "recorded instead of binning again" if records else ""),
+            "hbm": {"traffic_gbs": (assoc_traffic or 0.0) * launches_per / assoc_s / 1e9,
+                    "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": ((assoc_traffic or 0.0) * launches_per / assoc_s / 1e9) / peaks.get("hbm_gbs", 6800.0)}},
+    }
+    dom = max(roof, key=lambda k: roof[k]["ms_per_launch"])
+    other = [k for k in roof if k != dom][0]
+    ceilings = vote_ceilings(ht, g, batch, w, hit_votes, vote_s, vote_traffic * launches_per if vote_traffic else None,
+                             peaks, dev) if rank == 0 else None
     acc_bytes = 4.0 * g.n_phi * g.n_d0 * g.n_kappa * n_events
+    single = cpu_single_thread_finish(single_proc) if single_proc is not None else None
+    flips = None
+    if single and "flip_fraction_plain_fp32" in single:
+        flips = {"binary64_definition_gpu": 0.0,
+                 "gpu_basis": "the bin is defined in binary64; the GPU reproduces it bit for bit (parity tests), "
+                              "so its disagreement with an FP64 evaluation is 0",
+                 "plain_fp32_context": single.pop("flip_fraction_plain_fp32"), "bound": 1e-5}
     line = {
         "metric": METRIC, "value": world * n_events / (ms / 1e3), "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
@@ -617,26 +798,25 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "events_per_step": n_events, "hits_per_step": n_hits,
                    "grid": [g.n_phi, g.n_d0, g.n_kappa], "threshold": w.threshold, "window": w.window,
                    "mode": "batched persistent + CUDA graph", "l2": "flushed between timed steps",
-                   "parallelism": f"events sharded, {world} independent rank(s)", **tile},
+                   "parallelism": f"events sharded, {world} independent rank(s)", "waves": waves,
+                   "records": records, **tile},
         "hit_votes_per_s": world * hit_votes / (ms / 1e3),
         "peaks_per_step": int(counts[0]), "pairs_per_step": int(counts[1]),
-        "plain_events_per_s": plain_eps,
+        "plain_events_per_s": plain_eps, "plain_runs_ms": plain_runs, "plain_stat": "median of 5",
         "batched_over_plain": (n_events / (ms / 1e3)) / plain_eps,
         "phase_ms": {"vote": float(np.mean(vote_ms)), "peaks_assoc": float(np.mean(rest_ms)),
                      "assoc": float(np.mean(assoc_ms))},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops, "traffic": assoc_traffic,
-                     "kernel": "assoc_kernel", "ops_per_cell": ops_per_cell, "peak_basis": peak_basis},
-        "roofline_vote": {"bound": "alu", "achieved": achieved_vote, "peak": peak_tops, "unit": "Tops/s",
-                          "frac": achieved_vote / peak_tops, "traffic": vote_traffic,
-                          "kernel": "vote_band_kernel", "ops_per_cell": ops_per_cell, "peak_basis": peak_basis},
+        "roofline": roof[dom],
+        f"roofline_{other.split('_kernel')[0]}": roof[other],
         "ceilings_vote": ceilings,
         "hbm": {"step_bytes_min": 2 * acc_bytes + 8.0 * n_hits,
                 "achieved_gbs": (2 * acc_bytes + 8.0 * n_hits) / (ms / 1e3) / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src},
+        "flip_fraction": flips,
         "clocks": clk,
         "gpu_launches": int(launches) * args.steps,
         "e2e": e2e,
+        "secondary": secondary,
         "serving": serving,
         "range_vote": range_vote,
         "fit": fit_info,
@@ -644,8 +824,7 @@ def run_gpu(args):
         "vertex": vertex,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, batch)
-    ctx.close()
+        line["cpu_baseline"] = cpu_baseline(w, batch, single=single)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -669,7 +848,12 @@ def main():
     ap.add_argument("--tile", default="", help="vote tile 'phi,d0,threads' instead of autotuning")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed batched steps (no plain form, e2e or CPU baseline); for profiling")
+    ap.add_argument("--record-budget-gb", type=float, default=160.0,
+                    help="device memory for the vote records (GB); the 4096-event batch needs about 132")
+    ap.add_argument("--cpu-single-thread", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_single_thread:
+        return cpu_single_thread_worker()
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -157,6 +157,8 @@ typedef struct {
                                       cell again; used with point voting, band pruning of the vote,
                                       n_kappa <= 255 and a vote tile of 32, 64, 128 or 256 cells
                                       (other cases, and 0, bin again).  Same rows either way. */
+#define HT_OPT_WAVES 19            /* read-only: waves (kernel sequences over groups of events) of the
+                                      last ht_process */
 #define HT_OPT_RECORD_BUDGET 18    /* device memory for those records in bytes (0 = 72 GB): a wave of
                                       events needs (its hits) x (vote tiles per event) x (cells per
                                       tile) bytes, and ht_process splits the batch into waves that fit

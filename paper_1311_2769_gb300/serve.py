@@ -181,6 +181,31 @@ class GpuExecutor:
             }
             self.state.append(st)
         self.max_hits, self.max_batch = max_hits, max_batch
+        self._reserve()
+
+    def _reserve(self):
+        """One batch of max_batch events holding max_hits hits (all at the
+        origin) per slot, so that every device buffer of the slot's context
+        reaches its largest size before the first request: growing a buffer
+        later would free and allocate device memory, which synchronises the
+        whole device in the middle of the trace."""
+        ht = self.ht
+        for st in self.state:
+            st["x"].zero_()
+            st["y"].zero_()
+            st["l"].zero_()
+            offs = np.linspace(0, self.max_hits, self.max_batch + 1).astype(np.int32)
+            st["o"].numpy()[: self.max_batch + 1] = offs
+            hits = ht.Hits.__new__(ht.Hits)
+            hits.arrays = (st["x"], st["y"], st["o"], st["l"])
+            hits.struct = ht.HtHits(st["x"].data_ptr(), st["y"].data_ptr(), None, st["l"].data_ptr(),
+                                    st["o"].data_ptr(), self.max_batch, ht.HT_HOST, self.max_hits)
+            st["ctx"].process(hits, self.thr, self.win, st["res"], st["stream"])
+            try:
+                st["ctx"].sync()
+            except ht.HtError as e:
+                if e.status != ht.HT_ERR_OVERFLOW:
+                    raise
 
     def submit(self, slot, events):
         torch, ht = self.torch, self.ht
@@ -254,11 +279,12 @@ class GpuExecutor:
             st["ctx"].close()
 
 
-def measure(rates, n_events=4000, slots=3, max_batch=256, budget_gb=40.0, pair_cap=1 << 28, peak_cap=1 << 23):
+def measure(rates, n_events=4000, slots=3, max_batch=256, budget_gb=40.0, pair_cap=1 << 28, peak_cap=1 << 23,
+            max_hits=1 << 21):
     """p50/p99 latency and throughput of the trigger loop at each offered load."""
     w = synth.WORKLOADS["serving_lognormal"]
     ex = GpuExecutor(w.grid, w.spec.layers, w.threshold, w.window, slots=slots, max_batch=max_batch,
-                     peak_cap=peak_cap, pair_cap=pair_cap)
+                     max_hits=max_hits, peak_cap=peak_cap, pair_cap=pair_cap)
     out = []
     try:
         for rate in rates:

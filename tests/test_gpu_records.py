@@ -198,3 +198,24 @@ def test_records_unsupported_shapes_bin_again(ht):
     ctx.set_option(ht.HT_OPT_TILE_D0, 12)
     assert ctx.get_option(ht.HT_OPT_RECORDS) == 0
     ctx.close()
+
+
+def test_phase_timing_over_waves_and_host_chunks(ht):
+    """Phase times are summed over waves, with graph replay (device results)
+    and with direct launches (host results copied wave by wave)."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=12, first_event=900)
+    g = w.grid
+    for device_io in (True, False):
+        ctx = ht.Context(g, synth.LAYERS_13)
+        ctx.set_option(ht.HT_OPT_PHASE_TIMING, 1)
+        ctx.set_option(ht.HT_OPT_RECORD_BUDGET, b.n_hits * g.n_phi * g.n_d0 // 3)
+        hits = ht.Hits.from_batch(b, device="cuda" if device_io else None)
+        res = ht.Results(1 << 22, 1 << 27, device="cuda" if device_io else None)
+        for _ in range(2):
+            ctx.process(hits, w.threshold, w.window, res)
+            ctx.sync()
+        assert ctx.get_option(ht.HT_OPT_WAVES) >= 3
+        v, r, total, a = ctx.phase_times()
+        assert v > 0 and r > 0 and 0 < a <= r and v + r <= total * 1.05
+        ctx.close()
