@@ -1078,12 +1078,6 @@ int ht_create(const ht_geometry* geometry, const ht_grid* grid, ht_ctx** out) {
         ht_destroy(ctx);
         return st;
     }
-    if (detect_smem(grid->n_phi, grid->n_d0, grid->n_kappa) > 227 * 1024 ||
-        detect_prepare(grid->n_phi, grid->n_d0, grid->n_kappa) != cudaSuccess) {
-        cudaGetLastError();
-        ht_destroy(ctx);
-        return HT_ERR_INVALID_ARG;
-    }
     *out = ctx;
     return HT_OK;
 }
@@ -1208,9 +1202,6 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
                 return fail(ctx, HT_ERR_INVALID_ARG, "line voting needs a grid with n_kappa = 1");
             const bool line = value == HT_VOTE_LINE;
             const int pnd = line ? 1 : ctx->grid.n_d0, pnk = line ? ctx->grid.n_d0 : ctx->grid.n_kappa;
-            if (detect_smem(ctx->grid.n_phi, pnd, pnk) > 227 * 1024)
-                return fail(ctx, HT_ERR_INVALID_ARG, "peak detection tile does not fit shared memory");
-            CU(detect_prepare(ctx->grid.n_phi, pnd, pnk));
             ctx->vote_mode = (int)value;
             ctx->pnd = pnd;
             ctx->pnk = pnk;

@@ -131,8 +131,6 @@ cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer,
                             cudaStream_t s);
 cudaError_t launch_order(const int32_t* offs, int32_t event0, int32_t n_events, int64_t n_hits,
                          int32_t* order, cudaStream_t s);
-size_t detect_smem(int nphi, int nd, int nk);
-cudaError_t detect_prepare(int nphi, int nd, int nk);
 cudaError_t launch_detect(const PeakParams& p, cudaStream_t s);
 cudaError_t launch_emit(const PeakParams& p, cudaStream_t s);
 cudaError_t launch_paircount(const PeakParams& p, const int64_t* lo_dev, const int64_t* hi_dev,

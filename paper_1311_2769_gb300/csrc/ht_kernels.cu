@@ -657,130 +657,306 @@ __global__ void order_kernel(const int32_t* offs, int32_t event0, int32_t n_even
 }
 
 // ---------------------------------------------------------------------------
-// peaks: detection (warp per (event, phi0, d0) column, lanes over kappa)
+// peaks: detection by running maxima
 // ---------------------------------------------------------------------------
-// A CTA stages rows i0-1 .. i0+R (phi wraps) x columns j0-1 .. j0+TD of one
-// event in shared memory, cells outside the d0 range marked absent, and tests
-// every interior cell at or above the threshold against its 26 neighbours
-// with the linear-order tie rule.
-constexpr uint32_t kAbsent = 0xFFFFFFFFu;
+// The 26 neighbours of cell (i, j, k) split into the plane of row i - 1, the
+// plane of row i + 1, the columns (i, j - 1) and (i, j + 1), and the bins
+// k - 1 and k + 1 of the cell's own column.  With K(r, c) the maximum of
+// bins k - 1..k + 1 of column (r, c) and P(r) = max(K(r, j - 1), K(r, j),
+// K(r, j + 1)), the earlier neighbours' maximum is
+//   max(P(i - 1) if row i - 1 precedes row i, P(i + 1) if row i + 1 precedes
+//       row i (the phi wrap at the last row), K(i, j - 1), A(i, j, k - 1))
+// and the later neighbours' maximum the same with the other rows, K(i, j + 1)
+// and A(i, j, k + 1); absent neighbours read -1.  A warp takes one (event,
+// phi row, 32-bin kappa chunk), lanes over kappa, and walks the d0 columns
+// in order, keeping K of rows i - 1, i, i + 1 at three consecutive columns in
+// registers: each step loads one new column of each row (one coalesced load
+// plus the chunk's two halo bins).  It writes the chunk's peak word and its
+// population count; detect_words_kernel turns the counts into per-word
+// prefixes and the column's total.
+// One column of one row, a warp's 32-bin kappa chunk: the raw loads (issued
+// a step ahead) and their 3-bin maxima.  Lane 0 and lane 31 also load the
+// chunk's halo bins k0 - 1 and k0 + 32.
+struct ColRaw {
+    int a, h;
+};
 
-// shared column stride of the detection tile: kappa bins plus a pad that
-// keeps 16-byte rows for vector staging and shifts neighbour columns' banks
-__host__ __device__ __forceinline__ int detect_stride(int nk) { return (nk & 3) == 0 ? nk + 4 : nk + 1; }
+__device__ __forceinline__ ColRaw col_load(const uint32_t* colp, int k, int nk, int lane) {
+    ColRaw r;
+    r.a = k < nk ? (int)__ldg(colp + k) : -1;
+    const int hk = lane == 0 ? k - 1 : k + 1;
+    r.h = ((lane == 0 || lane == 31) && hk >= 0 && hk < nk) ? (int)__ldg(colp + hk) : -1;
+    return r;
+}
 
-__global__ void __launch_bounds__(512) detect_kernel(const PeakParams p, const int R, const int TD) {
-    extern __shared__ __align__(16) uint32_t tile[];
-    const int nk = p.nk, nkw = p.nkw;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int tcols = TD + 2;
-    const int cs = detect_stride(nk);  // padded column stride: neighbour columns fall in different banks
-    const int tiles_i = (p.nphi + R - 1) / R, tiles_j = (p.nd + TD - 1) / TD;
-    const int64_t items = (int64_t)p.n_events * tiles_i * tiles_j;
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int e = (int)(item / ((int64_t)tiles_i * tiles_j));
-        const int t = (int)(item - (int64_t)e * tiles_i * tiles_j);
-        const int ti = t / tiles_j, tj = t - (t / tiles_j) * tiles_j;
-        const int i0 = ti * R, j0 = tj * TD;
-        const int nr = min(R, p.nphi - i0), nj = min(TD, p.nd - j0);
+// a, its kappa neighbours am / ap (-1 when absent) and kx = max(am, a, ap)
+__device__ __forceinline__ void col_max(ColRaw r, int k, int nk, int lane, int& a, int& am, int& ap, int& kx) {
+    a = r.a;
+    am = __shfl_up_sync(0xffffffffu, a, 1);
+    ap = __shfl_down_sync(0xffffffffu, a, 1);
+    if (lane == 0) am = r.h;
+    if (lane == 31) ap = r.h;
+    if (k + 1 >= nk) ap = -1;
+    kx = max(a, max(am, ap));
+}
+
+// RB output rows per warp (rows i0 .. i0 + RB - 1 and their two neighbour
+// rows, loaded once per column step for all of them).
+template <int RB>
+__global__ void __launch_bounds__(256) detect_slide_kernel(const PeakParams p) {
+    constexpr int NR = RB + 2;  // rows i0 - 1 .. i0 + RB
+    const int lane = threadIdx.x & 31;
+    const int nk = p.nk, nkw = p.nkw, nd = p.nd, nphi = p.nphi;
+    const int nblk = (nphi + RB - 1) / RB;
+    const int64_t items = (int64_t)p.n_events * nblk * nkw;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < items; item += nwarps) {
+        const int kc = (int)(item % nkw);
+        const int64_t eb = item / nkw;
+        const int ib = (int)(eb % nblk);
+        const int e = (int)(eb / nblk);
+        const int i0 = ib * RB;
+        const int nout = min(RB, nphi - i0);
+        const int k = kc * 32 + lane;
         const uint32_t* A = p.acc + (int64_t)e * p.cells;
-        __syncthreads();
-        // stage (nr + 2) x (nj + 2) columns, warp by warp in row-major order
-        int ri = 0, cj = warp;
-        while (cj >= nj + 2) {
-            cj -= nj + 2;
-            ++ri;
+        const uint32_t* R[NR];
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            int r = i0 - 1 + t;
+            r = ((r % nphi) + nphi) % nphi;
+            R[t] = A + (int64_t)r * nd * nk;
         }
-        for (; ri < nr + 2;) {
-            int ii = i0 - 1 + ri;
-            ii = ii < 0 ? ii + p.nphi : (ii >= p.nphi ? ii - p.nphi : ii);
-            const int jj = j0 - 1 + cj;
-            uint32_t* dst = tile + (ri * tcols + cj) * cs;
-            if (jj < 0 || jj >= p.nd) {
-                for (int kk = lane; kk < nk; kk += 32) dst[kk] = kAbsent;
-            } else {
-                const uint32_t* src = A + ((int64_t)ii * p.nd + jj) * nk;
-                if ((nk & 3) == 0) {
-                    const uint4* s4 = reinterpret_cast<const uint4*>(src);
-                    uint4* d4 = reinterpret_cast<uint4*>(dst);
-                    for (int kk = lane; kk < (nk >> 2); kk += 32) d4[kk] = s4[kk];
+        // window per row: K at columns j - 1, j, j + 1; own bins at column j
+        int K0[NR], K1[NR], K2[NR];
+        int a1[NR], am1[NR], ap1[NR];
+        ColRaw nx[NR];
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            K0[t] = -1;
+            col_max(col_load(R[t], k, nk, lane), k, nk, lane, a1[t], am1[t], ap1[t], K1[t]);
+            nx[t] = nd > 1 ? col_load(R[t] + nk, k, nk, lane) : ColRaw{-1, -1};
+        }
+        const int64_t col0 = ((int64_t)e * nphi + i0) * nd;
+        for (int j = 0; j < nd; ++j) {
+            int a2[NR], am2[NR], ap2[NR];
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                if (j + 1 < nd) {
+                    col_max(nx[t], k, nk, lane, a2[t], am2[t], ap2[t], K2[t]);
                 } else {
-                    for (int kk = lane; kk < nk; kk += 32) dst[kk] = src[kk];
+                    a2[t] = am2[t] = ap2[t] = K2[t] = -1;
                 }
+                // the loads of column j + 2 are in flight during this step
+                nx[t] = j + 2 < nd ? col_load(R[t] + (int64_t)(j + 2) * nk, k, nk, lane) : ColRaw{-1, -1};
             }
-            cj += nw;
-            while (cj >= nj + 2) {
-                cj -= nj + 2;
-                ++ri;
-            }
-        }
-        __syncthreads();
-        // interior columns: warp per (row, column), lanes over kappa.  Every lane
-        // reads its 3x3x3 box (absent neighbours read as -1 in int32, so they
-        // never reject) and compares against the maximum of the neighbours that
-        // precede it in linear order (strictly) and of those that follow it.
-        int r = 0, j = warp;
-        while (j >= nj) {
-            j -= nj;
-            ++r;
-        }
-        for (; r < nr; j += nw) {
-            while (j >= nj) {
-                j -= nj;
-                ++r;
-            }
-            if (r >= nr) break;
-            const int i = i0 + r;
-            const int64_t col = ((int64_t)e * p.nphi + i) * p.nd + (j0 + j);
-            // row di = -1 / +1 precedes row i unless the phi wrap makes it follow
-            // (one row only: those rows are the row itself, covered by di = 0)
-            const bool single = p.nphi == 1;
-            const bool m_earlier = i > 0, p_earlier = i == p.nphi - 1;
-            int count = 0;
-            for (int k0 = 0, w = 0; k0 < nk; k0 += 32, ++w) {
-                const int kk = k0 + lane;
-                bool pk = false;
-                if (kk < nk) {
-                    const int v = (int)tile[((r + 1) * tcols + (j + 1)) * cs + kk];
-                    int mE = -1, mL = -1;
 #pragma unroll
-                    for (int di = -1; di <= 1; ++di) {
-                        if (single && di != 0) continue;
-                        const int* rowp = reinterpret_cast<const int*>(tile) + ((r + 1 + di) * tcols) * cs;
-#pragma unroll
-                        for (int dj = -1; dj <= 1; ++dj) {
-                            const int* cp2 = rowp + (j + 1 + dj) * cs;
-                            const int u0 = cp2[kk];
-                            const int um = kk > 0 ? cp2[kk - 1] : -1;
-                            const int up = kk + 1 < nk ? cp2[kk + 1] : -1;
-                            if (di == 0) {
-                                if (dj < 0) {
-                                    mE = max(mE, max(u0, max(um, up)));
-                                } else if (dj > 0) {
-                                    mL = max(mL, max(u0, max(um, up)));
-                                } else {
-                                    mE = max(mE, um);
-                                    mL = max(mL, up);
-                                }
-                            } else {
-                                const int m3 = max(u0, max(um, up));
-                                const bool earlier = di < 0 ? m_earlier : p_earlier;
-                                if (earlier) mE = max(mE, m3);
-                                else mL = max(mL, m3);
-                            }
-                        }
+            for (int o = 0; o < RB; ++o) {
+                if (o < nout) {  // warp-uniform
+                    const int i = i0 + o;
+                    const int c = o + 1;  // window row of output row i
+                    const bool planes = nphi > 1;  // one row: the planes are the cell's own column
+                    const int Pm = planes ? max(K0[c - 1], max(K1[c - 1], K2[c - 1])) : -1;
+                    const int Pp = planes ? max(K0[c + 1], max(K1[c + 1], K2[c + 1])) : -1;
+                    const bool m_earlier = i > 0, p_earlier = i == nphi - 1;
+                    const int E = max(max(m_earlier ? Pm : -1, p_earlier ? Pp : -1), max(K0[c], am1[c]));
+                    const int L = max(max(m_earlier ? -1 : Pm, p_earlier ? -1 : Pp), max(K2[c], ap1[c]));
+                    const int v = a1[c];
+                    const bool pk = k < nk && (uint32_t)v >= p.thr && v > E && v >= L;
+                    const unsigned b = __ballot_sync(0xffffffffu, pk);
+                    if (lane == 0) {
+                        const int64_t col = col0 + (int64_t)o * nd + j;
+                        p.mask[col * nkw + kc] = b;
+                        p.wpre[col * nkw + kc] = (uint16_t)__popc(b);
                     }
-                    pk = (uint32_t)v >= p.thr && v > mE && v >= mL;
                 }
-                const unsigned b = __ballot_sync(0xffffffffu, pk);
-                if (lane == 0) {
-                    p.mask[col * nkw + w] = b;
-                    p.wpre[col * nkw + w] = (uint16_t)count;
-                }
-                count += __popc(b);
             }
-            if (lane == 0) p.npk[col] = count;
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                K0[t] = K1[t];
+                K1[t] = K2[t];
+                a1[t] = a2[t];
+                am1[t] = am2[t];
+                ap1[t] = ap2[t];
+            }
         }
+    }
+}
+
+// The same rule with 16-byte loads (n_kappa a multiple of 4): lane L holds
+// bins c*128 + 4L .. c*128 + 4L + 3 of a 128-bin chunk c, so a warp covers
+// a 128-bin chunk of a column with one load; a bin's kappa neighbours come
+// from the lane's own registers and one shuffle each way (lanes 0 and 31
+// load the chunk's halo bins).  Peak bits are gathered into 32-bit words by
+// three xor shuffles over each group of eight lanes.  RB output rows per
+// warp, loads a column ahead.
+struct Col4 {
+    int v[4];
+    int h;  // halo: lane 0 bin c*128 - 1, lane 31 bin c*128 + 128
+};
+
+__device__ __forceinline__ Col4 col4_load(const uint32_t* colp, int kb, int nk, int lane) {
+    Col4 r;
+    if (kb < nk) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(colp + kb));
+        r.v[0] = (int)q.x;
+        r.v[1] = (int)q.y;
+        r.v[2] = (int)q.z;
+        r.v[3] = (int)q.w;
+    } else {
+        r.v[0] = r.v[1] = r.v[2] = r.v[3] = -1;
+    }
+    const int hk = lane == 0 ? kb - 1 : kb + 4;
+    r.h = ((lane == 0 || lane == 31) && hk >= 0 && hk < nk) ? (int)__ldg(colp + hk) : -1;
+    return r;
+}
+
+// kappa 3-bin maxima of the lane's four bins; lf / rt: the bins just left
+// of the first and right of the last (-1 when absent)
+__device__ __forceinline__ void col4_max(const Col4& c, int lane, int* K, int& lf, int& rt) {
+    lf = __shfl_up_sync(0xffffffffu, c.v[3], 1);
+    rt = __shfl_down_sync(0xffffffffu, c.v[0], 1);
+    if (lane == 0) lf = c.h;
+    if (lane == 31) rt = c.h;
+    const int m01 = max(c.v[0], c.v[1]), m12 = max(c.v[1], c.v[2]), m23 = max(c.v[2], c.v[3]);
+    K[0] = max(lf, m01);
+    K[1] = max(m01, c.v[2]);
+    K[2] = max(c.v[1], m23);
+    K[3] = max(m23, rt);
+}
+
+template <int RB>
+__global__ void __launch_bounds__(128) detect_vec_kernel(const PeakParams p) {
+    constexpr int NR = RB + 2;  // rows i0 - 1 .. i0 + RB
+    const int lane = threadIdx.x & 31;
+    const int nk = p.nk, nkw = p.nkw, nd = p.nd, nphi = p.nphi;
+    const int nch = (nk + 127) >> 7;
+    const int nblk = (nphi + RB - 1) / RB;
+    const int64_t items = (int64_t)p.n_events * nblk * nch;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < items; item += nwarps) {
+        const int ch = (int)(item % nch);
+        const int64_t eb = item / nch;
+        const int ib = (int)(eb % nblk);
+        const int e = (int)(eb / nblk);
+        const int i0 = ib * RB;
+        const int nout = min(RB, nphi - i0);
+        const int kb = ch * 128 + 4 * lane;
+        const uint32_t* A = p.acc + (int64_t)e * p.cells;
+        const uint32_t* R[NR];
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+            int r = i0 - 1 + t;
+            r = ((r % nphi) + nphi) % nphi;
+            R[t] = A + (int64_t)r * nd * nk;
+        }
+        const bool planes = nphi > 1;  // one row: the planes are the cell's own column
+        // window: K at columns j - 1 (0), j (1), j + 1 (2) for every row;
+        // the own bins' neighbours of the output rows at column j
+        int K[3][NR][4];
+        int own[RB][4], lfo[RB], rto[RB];
+        Col4 nx[NR];
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) K[0][t][q] = -1;
+            const Col4 c0 = col4_load(R[t], kb, nk, lane);
+            int lf, rt;
+            col4_max(c0, lane, K[1][t], lf, rt);
+            if (t >= 1 && t <= RB) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) own[t - 1][q] = c0.v[q];
+                lfo[t - 1] = lf;
+                rto[t - 1] = rt;
+            }
+            nx[t] = nd > 1 ? col4_load(R[t] + nk, kb, nk, lane) : Col4{{-1, -1, -1, -1}, -1};
+        }
+        const int64_t col0 = ((int64_t)e * nphi + i0) * nd;
+        for (int j = 0; j < nd; ++j) {
+            int own2[RB][4], lf2[RB], rt2[RB];
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                int lf = -1, rt = -1;
+                if (j + 1 < nd) {
+                    col4_max(nx[t], lane, K[2][t], lf, rt);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) K[2][t][q] = -1;
+                }
+                if (t >= 1 && t <= RB) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) own2[t - 1][q] = j + 1 < nd ? nx[t].v[q] : -1;
+                    lf2[t - 1] = lf;
+                    rt2[t - 1] = rt;
+                }
+                // the loads of column j + 2 are in flight during this step
+                nx[t] = j + 2 < nd ? col4_load(R[t] + (int64_t)(j + 2) * nk, kb, nk, lane)
+                                   : Col4{{-1, -1, -1, -1}, -1};
+            }
+#pragma unroll
+            for (int o = 0; o < RB; ++o) {
+                if (o < nout) {  // warp-uniform
+                    const int i = i0 + o;
+                    const int c = o + 1;
+                    const bool m_earlier = i > 0, p_earlier = i == nphi - 1;
+                    unsigned nib = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int Pm = planes ? max(K[0][c - 1][q], max(K[1][c - 1][q], K[2][c - 1][q])) : -1;
+                        const int Pp = planes ? max(K[0][c + 1][q], max(K[1][c + 1][q], K[2][c + 1][q])) : -1;
+                        const int km = q == 0 ? lfo[o] : own[o][q - 1];   // bin k - 1 of the own column
+                        const int kp = q == 3 ? rto[o] : own[o][q + 1];   // bin k + 1
+                        const int E = max(max(m_earlier ? Pm : -1, p_earlier ? Pp : -1), max(K[0][c][q], km));
+                        const int L = max(max(m_earlier ? -1 : Pm, p_earlier ? -1 : Pp), max(K[2][c][q], kp));
+                        const int v = own[o][q];
+                        const bool pk = kb + q < nk && (uint32_t)v >= p.thr && v > E && v >= L;
+                        nib |= (unsigned)pk << q;
+                    }
+                    // lanes 8w .. 8w + 7 hold word ch * 4 + w
+                    unsigned word = nib << (4 * (lane & 7));
+                    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+                    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+                    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+                    const int w = ch * 4 + (lane >> 3);
+                    if ((lane & 7) == 0 && w < nkw) {
+                        const int64_t col = col0 + (int64_t)o * nd + j;
+                        p.mask[col * nkw + w] = word;
+                        p.wpre[col * nkw + w] = (uint16_t)__popc(word);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < NR; ++t)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    K[0][t][q] = K[1][t][q];
+                    K[1][t][q] = K[2][t][q];
+                }
+#pragma unroll
+            for (int o = 0; o < RB; ++o) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) own[o][q] = own2[o][q];
+                lfo[o] = lf2[o];
+                rto[o] = rt2[o];
+            }
+        }
+    }
+}
+
+// Per column: the words' peak counts (left in wpre by detect_slide_kernel)
+// become the count of peaks in the column's earlier words; npk the total.
+__global__ void detect_words_kernel(const PeakParams p) {
+    const int64_t ncols = (int64_t)p.n_events * p.nphi * p.nd;
+    const int nkw = p.nkw;
+    for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncols;
+         col += (int64_t)gridDim.x * blockDim.x) {
+        uint16_t* w = p.wpre + col * nkw;
+        int run = 0;
+        for (int t = 0; t < nkw; ++t) {
+            const int c = w[t];
+            w[t] = (uint16_t)run;
+            run += c;
+        }
+        p.npk[col] = run;
     }
 }
 
@@ -1748,35 +1924,21 @@ cudaError_t launch_order(const int32_t* offs, int32_t event0, int32_t n_events, 
     return cudaGetLastError();
 }
 
-// detect tile: R interior rows x TD interior columns, halo included, ~96 KB
-void detect_tile(int nphi, int nd, int nk, int* R, int* TD) {
-    const int64_t budget = 96 * 1024 / 4;  // words
-    const int64_t cs = detect_stride(nk);
-    int td = nd;
-    while (td > 1 && (int64_t)3 * (td + 2) * cs > budget) td = (td + 1) / 2;
-    int r = (int)(budget / ((int64_t)(td + 2) * cs)) - 2;
-    r = std::max(1, std::min(r, nphi));
-    *R = r;
-    *TD = td;
-}
-
-size_t detect_smem(int nphi, int nd, int nk) {
-    int R, TD;
-    detect_tile(nphi, nd, nk, &R, &TD);
-    return (size_t)(R + 2) * (TD + 2) * detect_stride(nk) * 4;
-}
-
-cudaError_t detect_prepare(int nphi, int nd, int nk) {
-    return allow_dynamic_smem(reinterpret_cast<const void*>(detect_kernel), (int)detect_smem(nphi, nd, nk));
-}
-
 cudaError_t launch_detect(const PeakParams& p, cudaStream_t s) {
-    if ((int64_t)p.n_events * p.nphi * p.nd == 0) return cudaSuccess;
-    int R, TD;
-    detect_tile(p.nphi, p.nd, p.nk, &R, &TD);
-    const int64_t items = (int64_t)p.n_events * ((p.nphi + R - 1) / R) * ((p.nd + TD - 1) / TD);
-    const int grid = (int)std::min<int64_t>(items, 152 * 8);
-    detect_kernel<<<grid, 512, detect_smem(p.nphi, p.nd, p.nk), s>>>(p, R, TD);
+    const int64_t ncols = (int64_t)p.n_events * p.nphi * p.nd;
+    if (ncols == 0) return cudaSuccess;
+    if ((p.nk & 3) == 0 && ((uintptr_t)p.acc & 15) == 0) {
+        constexpr int RB = 2;  // output phi rows per warp
+        const int64_t items = (int64_t)p.n_events * ((p.nphi + RB - 1) / RB) * ((p.nk + 127) / 128);
+        const int grid = (int)std::min<int64_t>((items + 3) / 4, 152 * 16);
+        detect_vec_kernel<RB><<<grid, 128, 0, s>>>(p);
+    } else {
+        constexpr int RB = 4;  // output phi rows per warp
+        const int64_t items = (int64_t)p.n_events * ((p.nphi + RB - 1) / RB) * p.nkw;  // one warp each
+        const int grid = (int)std::min<int64_t>((items + 7) / 8, 152 * 8);
+        detect_slide_kernel<RB><<<grid, 256, 0, s>>>(p);
+    }
+    detect_words_kernel<<<(int)std::min<int64_t>((ncols + 255) / 256, 152 * 8), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

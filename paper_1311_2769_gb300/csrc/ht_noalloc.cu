@@ -94,7 +94,6 @@ extern "C" int ht_peaks_noalloc(const ht_grid* grid, const uint32_t* acc, int32_
     if (cols > (int64_t)(HT_NOALLOC_SCRATCH_BYTES / (12u + 6u * (unsigned)nkw))) return HT_ERR_BUDGET;
     const Layout L = layout(cols, nkw);
     if (L.total > (size_t)HT_NOALLOC_SCRATCH_BYTES) return HT_ERR_BUDGET;
-    if (detect_smem(grid->n_phi, grid->n_d0, grid->n_kappa) > 227 * 1024) return HT_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
     if (scratch_for_current_device(&base) != cudaSuccess) return HT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -102,7 +101,6 @@ extern "C" int ht_peaks_noalloc(const ht_grid* grid, const uint32_t* acc, int32_
     // the scratch keeps the previous call's contents: clear what must start at zero
     if (cudaMemsetAsync(scal, 0, 8 * sizeof(int64_t), s) != cudaSuccess) return HT_ERR_CUDA;
     if (cols > 0) {
-        if (detect_prepare(grid->n_phi, grid->n_d0, grid->n_kappa) != cudaSuccess) return HT_ERR_CUDA;
         PeakParams p{};
         p.acc = acc;
         p.cells = (int64_t)grid->n_phi * grid->n_d0 * grid->n_kappa;
