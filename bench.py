@@ -522,6 +522,10 @@ def run_gpu(args):
     hits_d = ht.Hits.from_batch(batch, device=dev)
     if args.prune is not None:
         ctx.set_option(ht.HT_OPT_PRUNE, args.prune)
+    if args.hit_staging is not None:
+        ctx.set_option(ht.HT_OPT_HIT_STAGING, args.hit_staging)
+    if args.vote_items is not None:
+        ctx.set_option(ht.HT_OPT_VOTE_ITEMS, args.vote_items)
     if args.tile:
         for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
             ctx.set_option(k, int(v))
@@ -848,6 +852,8 @@ def main():
     ap.add_argument("--tile", default="", help="vote tile 'phi,d0,threads' instead of autotuning")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed batched steps (no plain form, e2e or CPU baseline); for profiling")
+    ap.add_argument("--hit-staging", type=int, default=None, help="HT_OPT_HIT_STAGING (default: the library's)")
+    ap.add_argument("--vote-items", type=int, default=None, help="HT_OPT_VOTE_ITEMS (default: the library's)")
     ap.add_argument("--record-budget-gb", type=float, default=160.0,
                     help="device memory for the vote records (GB); the 4096-event batch needs about 132")
     ap.add_argument("--cpu-single-thread", action="store_true", help=argparse.SUPPRESS)

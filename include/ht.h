@@ -157,6 +157,15 @@ typedef struct {
                                       cell again; used with point voting, band pruning of the vote,
                                       n_kappa <= 255 and a vote tile of 32, 64, 128 or 256 cells
                                       (other cases, and 0, bin again).  Same rows either way. */
+#define HT_OPT_VOTE_ITEMS 20       /* band-pruned point vote: 1 each warp expands 32 hits' bands into
+                                      (hit, d0 column) items and bins 32 items at a time; 0 (default)
+                                      bins every column of the hull of 32 queued hits' bands.  Same
+                                      accumulators either way; ht_autotune tries both. */
+#define HT_OPT_HIT_STAGING 21      /* 1: the band vote (HT_OPT_VOTE_ITEMS 0) copies each event's hits
+                                      into shared memory in 512-hit blocks with 1-D bulk copies (TMA),
+                                      double-buffered, instead of loading them per warp; used when x
+                                      and y are 16-byte aligned.  A copy that never completes (a bounded
+                                      wait) is reported as HT_ERR_TIMEOUT.  Default 0; same results. */
 #define HT_OPT_WAVES 19            /* read-only: waves (kernel sequences over groups of events) of the
                                       last ht_process */
 #define HT_OPT_RECORD_BUDGET 18    /* device memory for those records in bytes (0 = 72 GB): a wave of

@@ -115,6 +115,11 @@ struct ht_ctx {
     int64_t rec_budget = kDefaultRecBudget;
     bool r_rec = false;                    // the resolved vote tile supports records
     int r_rec_blocks_per_sm = 1;           // the record-writing vote's occupancy
+    int r_rec_variant = 3;                 // the record-writing vote kernel
+    int vote_items = 0;                    // band vote over (hit, column) items (1) or the hull of queued hits (0)
+    int hit_staging = 0;                   // hull band vote: hits staged into shared memory by bulk copies
+    bool r_stage = false;                  // staged variants prepared for the resolved tile
+    int r_stage_blocks_per_sm = 1, r_stage_rec_blocks_per_sm = 1, r_stage_smem = 0;
     int rc_threads = 128, rc_cap = 256, rc_blocks_per_sm = 1;
     size_t rc_warp_bytes = 0;
     bool use_rec = false;                  // the current ht_process associates through records
@@ -343,7 +348,7 @@ int resolve_tiles(ht_ctx* ctx) {
     // bands bound point votes only: range and line voting sweep every cell
     const bool band = !range && (ctx->prune & 1) && ctx->K.band_ok;
     ctx->a_band = !range && (ctx->prune & 2) && ctx->K.band_ok;
-    const int variant = ctx->vote_mode == HT_VOTE_RANGE ? 2 : (band ? 1 : 0);
+    const int variant = ctx->vote_mode == HT_VOTE_RANGE ? 2 : (band ? (ctx->vote_items ? 4 : 1) : 0);
     const int smem = vote_smem_bytes(tp, td, nk, thr, variant);
     if (smem > 227 * 1024)
         return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d needs %d B of shared memory", tp, td, nk, smem);
@@ -358,12 +363,31 @@ int resolve_tiles(ht_ctx* ctx) {
     ctx->r_threads = thr;
     ctx->r_smem = smem;
     ctx->r_blocks_per_sm = per_sm;
+    // staged hit loads (hull band vote): the same vote with 512-hit blocks
+    // copied into shared memory; chosen per call when x and y are 16-byte aligned
+    ctx->r_stage = false;
+    if (ctx->hit_staging && variant == 1) {
+        const int ssm = vote_smem_bytes(tp, td, nk, thr, 6);
+        int b6 = 0, b7 = 0;
+        if (ssm <= 227 * 1024 && vote_prepare(tp, nk, ssm, 6) == cudaSuccess &&
+            vote_occupancy(tp, nk, thr, ssm, &b6, 6) == cudaSuccess && b6 >= 1) {
+            ctx->r_stage = true;
+            ctx->r_stage_smem = ssm;
+            ctx->r_stage_blocks_per_sm = b6;
+            if (nk <= 255 && vote_prepare(tp, nk, ssm, 7) == cudaSuccess &&
+                vote_occupancy(tp, nk, thr, ssm, &b7, 7) == cudaSuccess)
+                ctx->r_stage_rec_blocks_per_sm = std::max(b7, 1);
+        }
+        cudaGetLastError();
+    }
     // records: the band vote writes each tile's bins, the association reads them
     ctx->r_rec = false;
-    if (ctx->records && variant == 1 && ctx->vote_mode == HT_VOTE_POINT && assoc_rec_supported(tp, td, nk)) {
+    if (ctx->records && (variant == 1 || variant == 4) && ctx->vote_mode == HT_VOTE_POINT &&
+        assoc_rec_supported(tp, td, nk)) {
         int rper = 0;
-        CU(vote_prepare(tp, nk, smem, 3));
-        CU(vote_occupancy(tp, nk, thr, smem, &rper, 3));
+        const int rv = variant == 4 ? 5 : 3;
+        CU(vote_prepare(tp, nk, smem, rv));
+        CU(vote_occupancy(tp, nk, thr, smem, &rper, rv));
         // row cursors: about four peaks per cell before a tile needs a second
         // pass over its records (the batch workload averages under two)
         const size_t fixed = assoc_rec_warp_smem(tp, td, nk, 0);
@@ -378,6 +402,7 @@ int resolve_tiles(ht_ctx* ctx) {
             ablocks >= 1) {
             ctx->r_rec = true;
             ctx->r_rec_blocks_per_sm = rper;
+            ctx->r_rec_variant = rv;
             ctx->rc_threads = athr_r;
             ctx->rc_cap = cap;
             ctx->rc_warp_bytes = wbytes;
@@ -597,6 +622,7 @@ VoteParams vote_params(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent)
     p.edtab = ctx->d_edtab;
     p.K = ctx->K;
     p.stats = ctx->count_stages ? ctx->d_stats : nullptr;
+    p.err = ctx->d_err;
     return p;
 }
 
@@ -612,13 +638,20 @@ int64_t rec_per_hit(const ht_ctx* ctx) {
 int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStream_t s) {
     if (ne <= 0) return HT_OK;
     VoteParams p = vote_params(ctx, event0, ne, persistent);
-    int variant = ctx->r_variant, per_sm = ctx->r_blocks_per_sm;
+    int variant = ctx->r_variant, per_sm = ctx->r_blocks_per_sm, smem = ctx->r_smem;
     if (ctx->use_rec && ctx->vote_mode == HT_VOTE_POINT) {
         p.rec = ctx->rec.p;
         p.rbits = ctx->rbits.p;
         p.rec_bytes = ctx->r_tile_phi * ctx->r_tile_d;
-        variant = 3;
+        variant = ctx->r_rec_variant;
         per_sm = ctx->r_rec_blocks_per_sm;
+    }
+    // staged hit blocks: bulk copies need 16-byte-aligned x and y
+    if (ctx->r_stage && (variant == 1 || variant == 3) && ((uintptr_t)ctx->cx & 15) == 0 &&
+        ((uintptr_t)ctx->cy & 15) == 0) {
+        variant = variant == 1 ? 6 : 7;
+        per_sm = variant == 6 ? ctx->r_stage_blocks_per_sm : ctx->r_stage_rec_blocks_per_sm;
+        smem = ctx->r_stage_smem;
     }
     if (ctx->vote_mode == HT_VOTE_LINE) {
         if (persistent) CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
@@ -630,9 +663,9 @@ int run_vote(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent, cudaStrea
         CU(launch_order(ctx->coffs, event0, ne, ctx->c_hits, ctx->order.p, s));
         CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int32_t), s));
         const int grid = std::min<int64_t>(p.n_items, (int64_t)ctx->sms * per_sm);
-        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, ctx->r_smem, s, variant));
+        CU(launch_vote(ctx->r_tile_phi, p, grid, ctx->r_threads, smem, s, variant));
     } else {
-        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, ctx->r_smem, s, variant));
+        CU(launch_vote(ctx->r_tile_phi, p, p.n_items, ctx->r_threads, smem, s, variant));
     }
     return HT_OK;
 }
@@ -973,6 +1006,10 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
 int read_err(ht_ctx* ctx) {
     int32_t err = 0;
     CU(cudaMemcpy(&err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (err & 16) {
+        CU(cudaMemset(ctx->d_err, 0, sizeof(int32_t)));
+        return fail(ctx, HT_ERR_TIMEOUT, "internal: a hit-block copy into shared memory did not complete");
+    }
     if (err & 8) {
         CU(cudaMemset(ctx->d_err, 0, sizeof(int32_t)));
         return fail(ctx, HT_ERR_CUDA, "internal: an association row through the angular index came out with "
@@ -1191,6 +1228,14 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "records must be 0 or 1");
             ctx->records = (int)value;
             break;
+        case HT_OPT_VOTE_ITEMS:
+            if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "vote items must be 0 or 1");
+            ctx->vote_items = (int)value;
+            break;
+        case HT_OPT_HIT_STAGING:
+            if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "hit staging must be 0 or 1");
+            ctx->hit_staging = (int)value;
+            break;
         case HT_OPT_RECORD_BUDGET:
             if (value < 0) return fail(ctx, HT_ERR_INVALID_ARG, "record budget < 0");
             ctx->rec_budget = value ? value : kDefaultRecBudget;
@@ -1226,7 +1271,7 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
     ctx->gvalid = false;
     if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS || key == HT_OPT_ATILE_PHI ||
         key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE || key == HT_OPT_VOTE_MODE || key == HT_OPT_ASSOC_CURSORS ||
-        key == HT_OPT_RECORDS) {
+        key == HT_OPT_RECORDS || key == HT_OPT_VOTE_ITEMS || key == HT_OPT_HIT_STAGING) {
         int st = resolve_tiles(ctx);
         if (st) return st;
     }
@@ -1253,6 +1298,8 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_ASSOC_INDEX: *value = ctx->assoc_index; break;
         case HT_OPT_LAUNCHES: *value = ctx->launches; break;
         case HT_OPT_RECORDS: *value = ctx->r_rec ? 1 : 0; break;
+        case HT_OPT_VOTE_ITEMS: *value = ctx->vote_items; break;
+        case HT_OPT_HIT_STAGING: *value = ctx->r_stage ? 1 : 0; break;
         case HT_OPT_RECORD_BUDGET: *value = ctx->rec_budget; break;
         case HT_OPT_WAVES: *value = ctx->wave_start.empty() ? 0 : (int64_t)ctx->wave_start.size() - 1; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
@@ -1464,7 +1511,8 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         key.vals[10] = ctx->count_stages * 2 + ctx->timing;
         key.vals[11] = ((int64_t)ctx->a_tile_phi << 40) | ((int64_t)ctx->a_tile_d << 20) | ((int64_t)ctx->a_cap << 2) |
                        (ctx->r_band ? 2 : 0) | (ctx->a_band ? 1 : 0) | ((int64_t)ctx->vote_mode << 60);
-        key.vals[12] = (ctx->use_rec ? 1 : 0) | ((int64_t)ctx->rc_cap << 1);
+        key.vals[12] = (ctx->use_rec ? 1 : 0) | ((int64_t)ctx->rc_cap << 1) | ((int64_t)ctx->r_variant << 40) |
+                       ((int64_t)ctx->r_stage << 48);
         if (!ctx->gvalid || !(key == ctx->gkey) || ctx->gwaves != ctx->wave_start) {
             if (ctx->gexec) {
                 cudaGraphExecDestroy(ctx->gexec);
@@ -1813,7 +1861,8 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
         const int64_t pcap = std::min<int64_t>(ctx->cells * ctx->c_events / 8 + 1024, 1LL << 27);
         const int64_t qcap = std::min<int64_t>(pcap * 64, 1LL << 31);
         float rbest = 1e30f;
-        int rp = 0, rd = 0, rt = 0;
+        int rp = 0, rd = 0, rt = 0, ri = ctx->vote_items;
+        const int save_items = ctx->vote_items;
         if (pk.ensure(pcap, nullptr) == cudaSuccess && po.ensure(pcap + 1, nullptr) == cudaSuccess &&
             hi.ensure(qcap, nullptr) == cudaSuccess && ctx->paircnt.ensure(pcap, &ctx->gen) == cudaSuccess) {
             const bool timing = ctx->timing;
@@ -1826,10 +1875,12 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
                     if (!assoc_rec_supported(tp, td, nk)) continue;
                     const int smem = vote_smem_bytes(tp, td, nk, 256, 3);
                     if (smem > 200 * 1024) continue;
-                    for (int thr : {128, 256}) {
+                    for (int cfg = 0; cfg < 4; ++cfg) {
+                        const int thr = (cfg & 1) ? 256 : 128, items = cfg >> 1;
                         ctx->tile_phi = tp;
                         ctx->tile_d = td;
                         ctx->threads = thr;
+                        ctx->vote_items = items;
                         if (resolve_tiles(ctx) || !ctx->r_rec) continue;
                         if (plan_waves(ctx, hits, epw, s) || ensure_timing_events(ctx, (int)ctx->wave_start.size() - 1))
                             continue;
@@ -1858,6 +1909,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
                             rp = tp;
                             rd = td;
                             rt = thr;
+                            ri = items;
                         }
                     }
                 }
@@ -1867,10 +1919,12 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
         pk.release();
         po.release();
         hi.release();
+        ctx->vote_items = save_items;
         if (rp) {
             ctx->tile_phi = rp;
             ctx->tile_d = rd;
             ctx->threads = rt;
+            ctx->vote_items = ri;
             ctx->gvalid = false;
             ctx->have_votes = ctx->have_peaks = ctx->have_results = false;
             return resolve_tiles(ctx);

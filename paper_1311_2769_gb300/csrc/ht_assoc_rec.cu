@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(128, 4) assoc_rec_kernel(const AssocParams p) 
         int RB0[SPHI];
 #pragma unroll
         for (int r = 0; r < SPHI; ++r) {
-            const int n_r = r < nrows ? __shfl_sync(0xffffffffu, rn, r) : 0;
+            const int rn_r = __shfl_sync(0xffffffffu, rn, r);
+            const int n_r = r < nrows ? rn_r : 0;
             RG[r] = __shfl_sync(0xffffffffu, rg, r);
             RB0[r] = tot;
             if (lane == r) run_base = tot;

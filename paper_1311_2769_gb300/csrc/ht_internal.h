@@ -40,6 +40,7 @@ struct VoteParams {
     uint8_t* rec;
     uint32_t* rbits;
     int32_t rec_bytes;
+    int32_t* err;          // staged hit loads: bit 16 when a block copy did not complete
 };
 
 struct PeakParams {
@@ -118,8 +119,10 @@ struct ScanRange {
 constexpr int kScanBlocks = 304;
 constexpr int kScanThreads = 1024;
 
-// vote kernel variants: 0 full sweep, 1 d0-band compaction, 2 range voting,
-// 3 d0-band compaction writing vote records
+// vote kernel variants: 0 full sweep, 1 d0-band compaction (hull of queued
+// hits), 2 range voting, 3 = 1 writing vote records, 4 d0 bands as
+// (hit, column) items, 5 = 4 writing vote records, 6 = 1 and 7 = 3 with the
+// hits staged into shared memory by bulk copies
 int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant);
 cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes, int variant);
 cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant);

@@ -82,11 +82,9 @@ struct TileHit {
 // without a hit stay in the loop (the full-mask vote needs all 32) but are
 // masked.
 template <int SPHI, int NK, bool TAIL>
-__device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* cp, const float* sp,
-                                             const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
-                                             int nk, int64_t h, bool valid) {
-    const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
-    const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
+__device__ __forceinline__ void vote_xy(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
+                                        uint32_t* acc_s, uint32_t acc_sh, int ja, int jb, int nk, float x, float y,
+                                        bool valid) {
     const HitFast hf = hit_fast(x, y, p.K);
     const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
     float q[SPHI], qs[SPHI];
@@ -127,6 +125,15 @@ __device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* c
     }
 }
 
+template <int SPHI, int NK, bool TAIL>
+__device__ __forceinline__ void vote_one_hit(const VoteParams& p, const float* cp, const float* sp,
+                                             const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
+                                             int nk, int64_t h, bool valid) {
+    const float x = (!TAIL || valid) ? p.x[h] : 0.0f;
+    const float y = (!TAIL || valid) ? p.y[h] : 0.0f;
+    vote_xy<SPHI, NK, TAIL>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid);
+}
+
 // Packed bins of one column's SPHI cells (one byte per phi row, row 0 in
 // the lowest byte; 255: no vote).
 template <int SPHI> struct RecWord { using T = uint32_t; };
@@ -139,12 +146,10 @@ template <> struct RecWord<8> { using T = unsigned long long; };
 // columns outside the warp's hull 255 (a hit votes nowhere outside its own
 // band, and the hull contains it).  `rec` is the lane's record (valid lanes).
 template <int SPHI, int NK>
-__device__ __forceinline__ void vote_one_hit_rec(const VoteParams& p, const float* cp, const float* sp,
-                                                 const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
-                                                 int nk, int64_t h, bool valid, uint8_t* rec) {
+__device__ __forceinline__ void vote_xy_rec(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
+                                            uint32_t* acc_s, uint32_t acc_sh, int ja, int jb, int nk, float x, float y,
+                                            bool valid, uint8_t* rec) {
     using W = typename RecWord<SPHI>::T;
-    const float x = valid ? p.x[h] : 0.0f;
-    const float y = valid ? p.y[h] : 0.0f;
     const HitFast hf = hit_fast(x, y, p.K);
     const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
     float q[SPHI], qs[SPHI];
@@ -191,6 +196,15 @@ __device__ __forceinline__ void vote_one_hit_rec(const VoteParams& p, const floa
         }
         if (valid) rw[j] = word;
     }
+}
+
+template <int SPHI, int NK>
+__device__ __forceinline__ void vote_one_hit_rec(const VoteParams& p, const float* cp, const float* sp,
+                                                 const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
+                                                 int nk, int64_t h, bool valid, uint8_t* rec) {
+    const float x = valid ? p.x[h] : 0.0f;
+    const float y = valid ? p.y[h] : 0.0f;
+    vote_xy_rec<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid, rec);
 }
 
 template <int SPHI, int NK>
@@ -287,6 +301,98 @@ __global__ void __launch_bounds__(256, 3) vote_kernel(const VoteParams p) {
 // of a 4 x 16 tile have an empty band.
 constexpr int kHitQueue = 64;  // per-warp queue of banded hits (run 32 at a time)
 
+// ---- staged hit blocks: 1-D bulk copies (TMA) into shared memory ----------
+// One thread arms an mbarrier with the block's byte count and issues
+// cp.async.bulk copies of the block's 16-byte-aligned interior of x and of
+// y; every thread waits on the barrier's phase (a bounded wait), and a few
+// threads load the block's ragged ends (at most three hits each) directly.
+constexpr int kStageHits = 512;                 // hits per staged block
+constexpr int kStageBuf = kStageHits + 4;       // floats per array buffer (block start rounded down to 4)
+constexpr int kStageBytes = 2 * 2 * kStageBuf * 4;  // two buffers of x and y
+constexpr unsigned kStageWaitLimit = 1u << 20;  // try_wait rounds before a copy counts as lost
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// bounded wait for the completion of the barrier phase with parity `par`
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned par) {
+    for (unsigned i = 0; i < kStageWaitLimit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(par)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+struct StageBlock {
+    int64_t b0, b1, base, a0, a1;  // hits [b0, b1); smem index h - base; bulk part [a0, a1)
+};
+
+__device__ __forceinline__ StageBlock stage_block(int64_t hb, int64_t he, int b) {
+    StageBlock k;
+    k.b0 = hb + (int64_t)b * kStageHits;
+    k.b1 = clamp64(k.b0 + kStageHits, k.b0, he);
+    k.base = k.b0 & ~(int64_t)3;
+    k.a0 = clamp64((k.b0 + 3) & ~(int64_t)3, k.b0, k.b1);
+    k.a1 = clamp64(k.b1 & ~(int64_t)3, k.a0, k.b1);
+    return k;
+}
+
+// issued by one thread: block b of [hb, he) into buffer b & 1
+__device__ __forceinline__ void stage_issue(const VoteParams& p, float* stg, uint64_t* bars, int64_t hb, int64_t he,
+                                            int b) {
+    const StageBlock k = stage_block(hb, he, b);
+    uint64_t* bar = bars + (b & 1);
+    float* xs = stg + (b & 1) * 2 * kStageBuf;
+    float* ys = xs + kStageBuf;
+    if (k.a1 > k.a0) {
+        const unsigned bytes = (unsigned)((k.a1 - k.a0) * 4);
+        // the buffer's previous contents were read through the generic proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, 2 * bytes);
+        bulk_g2s(xs + (k.a0 - k.base), p.x + k.a0, bytes, bar);
+        bulk_g2s(ys + (k.a0 - k.base), p.y + k.a0, bytes, bar);
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+template <int SPHI, int NK, bool REC>
+__device__ __forceinline__ void vote_queued_xy(const VoteParams& p, const float* cp, const float* sp,
+                                               const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, const uint4* hq,
+                                               unsigned head, int n, int nj, int nk, int lane, uint8_t* rec_t,
+                                               int64_t hb) {
+    __syncwarp();
+    const bool valid = lane < n;
+    const uint4 ent = valid ? hq[(head + lane) & (kHitQueue - 1)] : make_uint4(0u, 0u, 0u, 0u);
+    const int lo = valid ? (int)(ent.y & 0xFFFFu) : nj, hi = valid ? (int)(ent.y >> 16) : -1;
+    const int ja = __reduce_min_sync(0xffffffffu, lo), jb = __reduce_max_sync(0xffffffffu, hi);
+    __syncwarp();  // entries read before their slots are reused
+    const float x = __uint_as_float(ent.z), y = __uint_as_float(ent.w);
+    if (REC)
+        vote_xy_rec<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid,
+                              rec_t + ((int64_t)ent.x - hb) * p.rec_bytes);
+    else
+        vote_xy<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid);
+}
+
 template <int SPHI, int NK, bool REC>
 __device__ __forceinline__ void vote_queued(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
                                             uint32_t* acc_s, uint32_t acc_sh, const uint2* hq, unsigned head, int n,
@@ -304,15 +410,29 @@ __device__ __forceinline__ void vote_queued(const VoteParams& p, const float* cp
         vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid);
 }
 
-template <int SPHI, int NK, bool REC>
+template <int SPHI, int NK, bool REC, bool STAGE>
 __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* dt_s = reinterpret_cast<float4*>(smem_raw);
     const int nthr = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    constexpr int QB = STAGE ? 16 : 8;  // queue entry: (hit, band) [+ x, y when staged]
     uint2* hq = reinterpret_cast<uint2*>(smem_raw + 16 * p.tile_d) + warp * kHitQueue;
-    uint32_t* acc_s = reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d + 8 * kHitQueue * nw);
+    uint4* hq4 = reinterpret_cast<uint4*>(smem_raw + 16 * p.tile_d) + warp * kHitQueue;
+    float* stg = reinterpret_cast<float*>(smem_raw + 16 * p.tile_d + QB * kHitQueue * nw);
+    uint32_t* acc_s =
+        reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d + QB * kHitQueue * nw + (STAGE ? kStageBytes : 0));
     __shared__ int s_item;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    unsigned par[2] = {0u, 0u};
+    if (STAGE) {
+        if (tid == 0) {
+            mbar_init(&s_bar[0], 1);
+            mbar_init(&s_bar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
 
     const int nk = NK ? NK : p.K.nk;
     const int tiles = p.tiles_phi * p.tiles_d;
@@ -372,11 +492,12 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
             bits_t = p.rbits + (((hb - whb) >> 5) + e) * (int64_t)tiles + (int64_t)t * ((he - hb + 31) >> 5);
         }
         unsigned head = 0, tail = 0;
-        for (int64_t c0 = hb + warp * 32; c0 < he; c0 += nthr) {
+        // one chunk of 32 hits: bands, the bitmap word, queueing and votes
+        auto chunk = [&](int64_t c0, int64_t cend, const float* xs, const float* ys, int64_t base) {
             const int64_t h = c0 + lane;
-            const bool valid = h < he;
-            const float x = valid ? p.x[h] : 0.0f;
-            const float y = valid ? p.y[h] : 0.0f;
+            const bool valid = h < cend;
+            const float x = valid ? (STAGE ? xs[h - base] : p.x[h]) : 0.0f;
+            const float y = valid ? (STAGE ? ys[h - base] : p.y[h]) : 0.0f;
             const float r2 = fmaf(x, x, __fmul_rn(y, y));
             int lo = nj, hi = -1;
 #pragma unroll
@@ -391,16 +512,304 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
             const bool keep = valid && hi >= lo;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (REC && lane == 0) bits_t[(c0 - hb) >> 5] = m;
-            if (keep) hq[(tail + __popc(m & lt)) & (kHitQueue - 1)] = make_uint2((unsigned)h, (unsigned)lo | ((unsigned)hi << 16));
+            const unsigned slot = (tail + __popc(m & lt)) & (kHitQueue - 1);
+            const unsigned band = (unsigned)lo | ((unsigned)hi << 16);
+            if (keep) {
+                if (STAGE)
+                    hq4[slot] = make_uint4((unsigned)h, band, __float_as_uint(x), __float_as_uint(y));
+                else
+                    hq[slot] = make_uint2((unsigned)h, band);
+            }
             tail += __popc(m);
             if (tail - head >= 32) {
-                vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, 32, nj, nk, lane, rec_t, hb);
+                if (STAGE)
+                    vote_queued_xy<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq4, head, 32, nj, nk, lane, rec_t, hb);
+                else
+                    vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, 32, nj, nk, lane, rec_t, hb);
                 head += 32;
             }
+        };
+        if (!STAGE) {
+            for (int64_t c0 = hb + warp * 32; c0 < he; c0 += nthr) chunk(c0, he, nullptr, nullptr, 0);
+        } else {
+            const int nblk = (int)((he - hb + kStageHits - 1) / kStageHits);
+            if (tid == 0) {
+                if (nblk > 0) stage_issue(p, stg, s_bar, hb, he, 0);
+                if (nblk > 1) stage_issue(p, stg, s_bar, hb, he, 1);
+            }
+            for (int b = 0; b < nblk; ++b) {
+                const int buf = b & 1;
+                const bool ok = mbar_wait(&s_bar[buf], par[buf]);
+                par[buf] ^= 1u;
+                const StageBlock k = stage_block(hb, he, b);
+                float* xs = stg + buf * 2 * kStageBuf;
+                float* ys = xs + kStageBuf;
+                if (tid < 3) {  // ragged head and tail, loaded directly
+                    const int64_t h = k.b0 + tid;
+                    if (h < k.a0) {
+                        xs[h - k.base] = p.x[h];
+                        ys[h - k.base] = p.y[h];
+                    }
+                } else if (tid < 6) {
+                    const int64_t h = k.a1 + (tid - 3);
+                    if (h < k.b1) {
+                        xs[h - k.base] = p.x[h];
+                        ys[h - k.base] = p.y[h];
+                    }
+                }
+                if (__syncthreads_or(!ok)) {
+                    // a copy never completed: report it, wait (bounded) for the
+                    // copies still in flight into this block's memory, leave
+                    if (tid == 0) {
+                        atomicOr(p.err, 16);
+                        mbar_wait(&s_bar[0], par[0]);
+                        mbar_wait(&s_bar[1], par[1]);
+                    }
+                    __syncthreads();
+                    return;
+                }
+                for (int64_t c0 = k.b0 + warp * 32; c0 < k.b1; c0 += nthr) chunk(c0, k.b1, xs, ys, k.base);
+                __syncthreads();  // the block's buffer is no longer read
+                if (tid == 0 && b + 2 < nblk) stage_issue(p, stg, s_bar, hb, he, b + 2);
+            }
         }
-        if (tail != head)
-            vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, (int)(tail - head), nj, nk, lane, rec_t,
-                                       hb);
+        if (tail != head) {
+            if (STAGE)
+                vote_queued_xy<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq4, head, (int)(tail - head), nj, nk, lane,
+                                              rec_t, hb);
+            else
+                vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, (int)(tail - head), nj, nk, lane,
+                                           rec_t, hb);
+        }
+        __syncthreads();
+
+        uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
+        const int nrj = nrows * nj;
+        for (int row = warp; row < nrj; row += nw) {
+            const int r = row / nj;
+            const int j = row - r * nj;
+            const uint32_t* src = acc_s + j * col_words + r * nk;
+            uint32_t* dst = dst_e + ((int64_t)(i0 + r) * p.K.nd + (j0 + j)) * nk;
+            if ((nk & 3) == 0) {
+                const uint4* s4 = reinterpret_cast<const uint4*>(src);
+                uint4* d4 = reinterpret_cast<uint4*>(dst);
+                for (int kk = lane; kk < (nk >> 2); kk += 32) d4[kk] = s4[kk];
+            } else {
+                for (int kk = lane; kk < nk; kk += 32) dst[kk] = src[kk];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pruned vote over (hit, column) items
+// ---------------------------------------------------------------------------
+// Each warp takes 32 consecutive hits of the item's event and computes their
+// d0 bands for the tile (the union over the tile's rows, as above).  The
+// band columns of those hits, in hit order, are the warp's work items; lanes
+// take them 32 at a time.  Every lane leaves its hit's per-hit values in the
+// warp's shared slot table and writes its lane number into the item map over
+// its band's items, so an item's lane reads its hit with one byte load and
+// four 16-byte loads.  No lane evaluates a column outside its hit's band,
+// whatever the mix of band widths.
+struct FlatHit {
+    float4 a;        // x, y, r2, G
+    float4 b;        // dmin, R1, (lo, first item) as int bits
+    float q[8];      // q per row (up to 8 rows)
+    float qs[8];     // q * S2 per row
+};
+
+__host__ __device__ constexpr int flat_slot_bytes(int sphi) { return 32 + 8 * ((sphi + 3) / 4 * 4); }
+
+template <int SPHI, int NK, bool REC>
+__global__ void __launch_bounds__(256, 3) vote_flat_kernel(const VoteParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* dt_s = reinterpret_cast<float4*>(smem_raw);
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    constexpr int QW = (SPHI + 3) / 4;  // float4s of q (and of qs) per slot
+    constexpr int SLOT = flat_slot_bytes(SPHI) / 16;  // float4s per slot
+    float4* slots = reinterpret_cast<float4*>(smem_raw + 16 * p.tile_d) + warp * 32 * SLOT;
+    uint8_t* imap = smem_raw + 16 * p.tile_d + 16 * SLOT * 32 * nw + warp * 32 * p.tile_d;
+    uint32_t* acc_s =
+        reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d + 16 * SLOT * 32 * nw + ((32 * p.tile_d * nw + 15) & ~15));
+    __shared__ int s_item;
+    using W = typename RecWord<SPHI>::T;
+
+    const int nk = NK ? NK : p.K.nk;
+    const int tiles = p.tiles_phi * p.tiles_d;
+    const int col_words = SPHI * nk;
+    const uint32_t acc_sh = smem_addr(acc_s);
+    const unsigned nku = (unsigned)nk;
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+
+    for (int it = 0;; ++it) {
+        int item;
+        if (p.queue) {
+            if (tid == 0) s_item = atomicAdd(p.queue, 1);
+            __syncthreads();
+            item = s_item;
+        } else {
+            if (it > 0) break;
+            item = p.item0 + blockIdx.x;
+        }
+        if (item >= p.n_items) break;
+        const int el = item / tiles;
+        const int t = item - el * tiles;
+        const int e = p.order ? p.order[el] : el;
+        const int tp = t / p.tiles_d;
+        const int td = t - tp * p.tiles_d;
+        const int i0 = tp * SPHI;
+        const int j0 = td * p.tile_d;
+        const int nj = min(p.tile_d, p.K.nd - j0);
+        const int nrows = min(SPHI, p.K.nphi - i0);
+        const int64_t hb = clamp64(p.offs[p.event0 + e], 0, p.n_hits);
+        const int64_t he = clamp64(p.offs[p.event0 + e + 1], hb, p.n_hits);
+
+        for (int w = tid; w < nj * col_words; w += nthr) acc_s[w] = 0u;
+        for (int j = tid; j < nj; j += nthr) dt_s[j] = p.dtab[j0 + j];
+        float cp[SPHI], sp[SPHI];
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            const int i = r < nrows ? i0 + r : i0;
+            cp[r] = p.cphi[i];
+            sp[r] = p.sphi[i];
+        }
+        if (p.stats && tid == 0) atomicAdd(&p.stats[0], (unsigned long long)((he - hb) * nrows * nj));
+        __syncthreads();
+
+        const float dlo = dt_s[0].x, dhi = dt_s[nj - 1].x;
+        uint8_t* rec_t = nullptr;
+        uint32_t* bits_t = nullptr;
+        if (REC) {
+            // within the wave's hits even for offsets the validation rejects
+            // (the records are sized for the wave)
+            const int64_t whb = clamp64(p.offs[p.event0], 0, p.n_hits);
+            const int64_t wend = clamp64(p.offs[p.event0 + p.n_events], whb, p.n_hits);
+            if (hb < whb || he > wend) {
+                __syncthreads();
+                continue;
+            }
+            rec_t = p.rec + ((hb - whb) * tiles + (int64_t)t * (he - hb)) * p.rec_bytes;
+            bits_t = p.rbits + (((hb - whb) >> 5) + e) * (int64_t)tiles + (int64_t)t * ((he - hb + 31) >> 5);
+        }
+        for (int64_t c0 = hb + warp * 32; c0 < he; c0 += nthr) {
+            const int64_t h = c0 + lane;
+            const bool valid = h < he;
+            const float x = valid ? p.x[h] : 0.0f;
+            const float y = valid ? p.y[h] : 0.0f;
+            const float r2 = fmaf(x, x, __fmul_rn(y, y));
+            float q[SPHI], qs[SPHI];
+            int lo = nj, hi = -1;
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                q[r] = q_of(x, y, cp[r], sp[r]);
+                qs[r] = q[r] * S2;
+                int jl, jh;
+                d0_band(r2, q[r], dlo, dhi, j0, nj, p.K, jl, jh);
+                if (jh >= jl) {
+                    lo = min(lo, jl - j0);
+                    hi = max(hi, jh - j0);
+                }
+            }
+            const bool keep = valid && hi >= lo;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (REC && lane == 0) bits_t[(c0 - hb) >> 5] = m;
+            if (m == 0u) continue;
+            const int width = keep ? hi - lo + 1 : 0;
+            int P = width;  // inclusive prefix of the band widths
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, P, o);
+                if (lane >= o) P += v;
+            }
+            const int Wtot = __shfl_sync(0xffffffffu, P, 31);
+            P -= width;  // exclusive
+            const HitFast hf = hit_fast(x, y, p.K);
+            __syncwarp();  // the previous chunk's slots and map are no longer read
+            {
+                float4* sl = slots + lane * SLOT;
+                sl[0] = make_float4(x, y, hf.r2, hf.G);
+                sl[1] = make_float4(hf.dmin, hf.R1, __int_as_float(lo), __int_as_float(P));
+#pragma unroll
+                for (int w4 = 0; w4 < QW; ++w4) {
+                    float4 a, b;
+                    a.x = 4 * w4 + 0 < SPHI ? q[4 * w4 + 0] : 0.0f;
+                    a.y = 4 * w4 + 1 < SPHI ? q[4 * w4 + 1] : 0.0f;
+                    a.z = 4 * w4 + 2 < SPHI ? q[4 * w4 + 2] : 0.0f;
+                    a.w = 4 * w4 + 3 < SPHI ? q[4 * w4 + 3] : 0.0f;
+                    b.x = 4 * w4 + 0 < SPHI ? qs[4 * w4 + 0] : 0.0f;
+                    b.y = 4 * w4 + 1 < SPHI ? qs[4 * w4 + 1] : 0.0f;
+                    b.z = 4 * w4 + 2 < SPHI ? qs[4 * w4 + 2] : 0.0f;
+                    b.w = 4 * w4 + 3 < SPHI ? qs[4 * w4 + 3] : 0.0f;
+                    sl[2 + w4] = a;
+                    sl[2 + QW + w4] = b;
+                }
+                for (int k = 0; k < width; ++k) imap[P + k] = (uint8_t)lane;
+            }
+            W* rw_own = REC ? reinterpret_cast<W*>(rec_t + (h - hb) * p.rec_bytes) : nullptr;
+            if (REC && keep) {
+                const W none = (W)~(W)0;
+                for (int j = 0; j < lo; ++j) rw_own[j] = none;
+                for (int j = hi + 1; j < p.tile_d; ++j) rw_own[j] = none;
+            }
+            __syncwarp();
+            for (int s0 = 0; s0 < Wtot; s0 += 32) {
+                const int itm = s0 + lane;
+                const bool act = itm < Wtot;
+                const int o = act ? imap[itm] : 0;
+                const float4* sl = slots + o * SLOT;
+                const float4 A0 = sl[0], A1 = sl[1];
+                const int j = act ? __float_as_int(A1.z) + (itm - __float_as_int(A1.w)) : 0;
+                float oq[SPHI], oqs[SPHI];
+#pragma unroll
+                for (int w4 = 0; w4 < QW; ++w4) {
+                    const float4 a = sl[2 + w4], b = sl[2 + QW + w4];
+                    if (4 * w4 + 0 < SPHI) { oq[4 * w4 + 0] = a.x; oqs[4 * w4 + 0] = b.x; }
+                    if (4 * w4 + 1 < SPHI) { oq[4 * w4 + 1] = a.y; oqs[4 * w4 + 1] = b.y; }
+                    if (4 * w4 + 2 < SPHI) { oq[4 * w4 + 2] = a.z; oqs[4 * w4 + 2] = b.z; }
+                    if (4 * w4 + 3 < SPHI) { oq[4 * w4 + 3] = a.w; oqs[4 * w4 + 3] = b.w; }
+                }
+                const float4 dt = dt_s[j];
+                const float Rj = A0.z + dt.z;
+                const uint32_t col_sh = acc_sh + 4u * (unsigned)(j * col_words);
+                bool und = false;
+                uint32_t wlo = 0, whi = 0;
+#pragma unroll
+                for (int r = 0; r < SPHI; ++r) {
+                    const S1 c = stage1_fast(oqs[r], oq[r], dt, Rj, A0.w, H, T0);
+                    const uint32_t addr = col_sh + 4u * ((unsigned)(r * nk) + c.kb);
+                    if (REC) {
+                        if (r < 4)
+                            wlo = red_and_byte(addr, c.flo, c.fhi, c.kb, nku, act, wlo, 8u * r);
+                        else
+                            whi = red_and_byte(addr, c.flo, c.fhi, c.kb, nku, act, whi, 8u * (r - 4));
+                    } else {
+                        red_if_vote(addr, c.flo, c.fhi, c.kb, nku, act);
+                    }
+                    und |= (c.flo != c.fhi) & act;
+                }
+                W word = (W)(SPHI == 8 ? ((unsigned long long)whi << 32) | wlo : wlo);
+                if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+                    for (int r = 0; r < SPHI; ++r) {
+                        const S1 c = stage1_fast(oqs[r], oq[r], dt, Rj, A0.w, H, T0);
+                        if ((c.flo != c.fhi) && act && stage1_pending(c, A1.x, p.K.wlo, p.K.whi)) {
+                            const int kk = cell_slow(A0.x, A0.y, cp[r], sp[r], dt.x, A1.y, p.K, p.stats);
+                            if (kk >= 0) atomicAdd(acc_s + j * col_words + r * nk + kk, 1u);
+                            if (REC)
+                                word = (word & ~((W)0xFF << (8 * r))) |
+                                       ((W)(kk >= 0 ? (unsigned)kk : 255u) << (8 * r));
+                        }
+                    }
+                }
+                if (REC && act) {
+                    W* rw = reinterpret_cast<W*>(rec_t + (c0 + o - hb) * p.rec_bytes);
+                    rw[j] = word;
+                }
+            }
+        }
         __syncthreads();
 
         uint32_t* dst_e = p.acc + (int64_t)e * p.cells;
@@ -1774,7 +2183,11 @@ __global__ void rcp_check_kernel(uint32_t first_bits, uint32_t count, unsigned l
 // launchers
 // ---------------------------------------------------------------------------
 int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant) {
-    const int queues = variant == 1 || variant == 3 ? (threads / 32) * kHitQueue * 8 : 0;
+    const int warps = threads / 32;
+    int queues = variant == 1 || variant == 3 ? warps * kHitQueue * 8 : 0;
+    if (variant == 6 || variant == 7) queues = warps * kHitQueue * 16 + kStageBytes;
+    // item vote: a slot per lane and an item map of 32 * tile_d bytes per warp
+    if (variant == 4 || variant == 5) queues = warps * 32 * flat_slot_bytes(tile_phi) + ((32 * tile_d * warps + 15) & ~15);
     const int table = variant == 2 ? 16 * (tile_d + 1) : 16 * tile_d;
     return table + queues + 4 * tile_phi * tile_d * nk;
 }
@@ -1805,20 +2218,23 @@ static void* vote_fn() {
     return reinterpret_cast<void*>(vote_kernel<S, N>);
 }
 template <int S, int N>
-static void* vote_band_fn(bool rec) {
-    return rec ? reinterpret_cast<void*>(vote_band_kernel<S, N, true>)
-               : reinterpret_cast<void*>(vote_band_kernel<S, N, false>);
+static void* vote_band_fn(bool rec, bool stage) {
+    if (stage)
+        return rec ? reinterpret_cast<void*>(vote_band_kernel<S, N, true, true>)
+                   : reinterpret_cast<void*>(vote_band_kernel<S, N, false, true>);
+    return rec ? reinterpret_cast<void*>(vote_band_kernel<S, N, true, false>)
+               : reinterpret_cast<void*>(vote_band_kernel<S, N, false, false>);
 }
 
 // records hold one byte per bin: only grids with n_kappa <= 255 write them
-static void* vote_band_instance(int tile_phi, int nk, bool rec) {
-#define HT_VOTEB_NK(S)                                     \
-    switch (nk) {                                          \
-        case 64: return vote_band_fn<S, 64>(rec);          \
-        case 128: return vote_band_fn<S, 128>(rec);        \
-        case 256: return vote_band_fn<S, 256>(false);      \
-        case 512: return vote_band_fn<S, 512>(false);      \
-        default: return vote_band_fn<S, 0>(rec && nk <= 255); \
+static void* vote_band_instance(int tile_phi, int nk, bool rec, bool stage = false) {
+#define HT_VOTEB_NK(S)                                              \
+    switch (nk) {                                                   \
+        case 64: return vote_band_fn<S, 64>(rec, stage);            \
+        case 128: return vote_band_fn<S, 128>(rec, stage);          \
+        case 256: return vote_band_fn<S, 256>(false, stage);        \
+        case 512: return vote_band_fn<S, 512>(false, stage);        \
+        default: return vote_band_fn<S, 0>(rec && nk <= 255, stage); \
     }
     switch (tile_phi) {
         case 1: HT_VOTEB_NK(1)
@@ -1874,11 +2290,41 @@ static void* vote_instance(int tile_phi, int nk) {
     return nullptr;
 }
 
-// variant 3: the band vote writing records
+template <int S, int N>
+static void* vote_flat_fn(bool rec) {
+    return rec ? reinterpret_cast<void*>(vote_flat_kernel<S, N, true>)
+               : reinterpret_cast<void*>(vote_flat_kernel<S, N, false>);
+}
+
+static void* vote_flat_instance(int tile_phi, int nk, bool rec) {
+#define HT_VOTEF_NK(S)                                     \
+    switch (nk) {                                          \
+        case 64: return vote_flat_fn<S, 64>(rec);          \
+        case 128: return vote_flat_fn<S, 128>(rec);        \
+        case 256: return vote_flat_fn<S, 256>(false);      \
+        case 512: return vote_flat_fn<S, 512>(false);      \
+        default: return vote_flat_fn<S, 0>(rec && nk <= 255); \
+    }
+    switch (tile_phi) {
+        case 1: HT_VOTEF_NK(1)
+        case 2: HT_VOTEF_NK(2)
+        case 4: HT_VOTEF_NK(4)
+        case 8: HT_VOTEF_NK(8)
+    }
+#undef HT_VOTEF_NK
+    return nullptr;
+}
+
+// variants: 0 full sweep, 1 band (hull of queued hits), 2 range, 3 = 1 writing
+// records, 4 band over (hit, column) items, 5 = 4 writing records
 static void* vote_variant(int tile_phi, int nk, int variant) {
-    return variant == 2 ? vote_range_instance(tile_phi, nk)
-                        : (variant == 1 || variant == 3 ? vote_band_instance(tile_phi, nk, variant == 3)
-                                                        : vote_instance(tile_phi, nk));
+    switch (variant) {
+        case 1: case 3: return vote_band_instance(tile_phi, nk, variant == 3);
+        case 6: case 7: return vote_band_instance(tile_phi, nk, variant == 7, true);
+        case 2: return vote_range_instance(tile_phi, nk);
+        case 4: case 5: return vote_flat_instance(tile_phi, nk, variant == 5);
+        default: return vote_instance(tile_phi, nk);
+    }
 }
 
 cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant) {

@@ -48,6 +48,8 @@ HT_OPT_ASSOC_INDEX = 16
 HT_OPT_RECORDS = 17
 HT_OPT_RECORD_BUDGET = 18
 HT_OPT_WAVES = 19
+HT_OPT_VOTE_ITEMS = 20
+HT_OPT_HIT_STAGING = 21
 HT_VOTE_POINT = 0
 HT_VOTE_RANGE = 1
 HT_VOTE_LINE = 2

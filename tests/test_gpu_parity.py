@@ -498,3 +498,83 @@ def test_overflow_across_waves(ht):
         m = min(qc, int(full[1][len(pk)]))
         assert np.array_equal(hi[:m], full[2][:m])
         ctx.close()
+
+
+@pytest.mark.parametrize("grid", [synth.WORKLOADS["batch_4096_lognormal"].grid,
+                                  synth.Grid(96, 24, 64, -25.0, 25.0, -0.0114, 0.0114),
+                                  synth.Grid(50, 17, 40, -7.0, 30.0, -0.02, 0.005)])
+def test_vote_items_equal_hull_vote(ht, oracle_mod, grid):
+    """The band vote over (hit, column) items gives the accumulators of the
+    hull vote and of the oracle, and the same CSR with and without records."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=4, first_event=33)
+    accs = []
+    for items in (1, 0):
+        ctx = ht.Context(grid, w.spec.layers)
+        ctx.set_option(ht.HT_OPT_VOTE_ITEMS, items)
+        assert ctx.get_option(ht.HT_OPT_VOTE_ITEMS) == items
+        ctx.vote(ht.Hits.from_batch(b, device="cuda"))
+        accs.append([ctx.accumulator(e) for e in range(b.n_events)])
+        ctx.close()
+    acc_o = oracle_mod.vote(grid, b.x, b.y, b.event_offsets)
+    for e in range(b.n_events):
+        assert np.array_equal(accs[0][e], acc_o[e]) and np.array_equal(accs[1][e], acc_o[e])
+    outs = [_run(ht, grid, b, 5, 1, opts=((ht.HT_OPT_VOTE_ITEMS, it), (ht.HT_OPT_RECORDS, rec)))
+            for it, rec in ((1, 1), (0, 1), (1, 0))]
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(a, c)
+    assert np.array_equal(outs[0][0], oracle_mod.peaks(grid, acc_o, 5))
+    _check_csr_rows(oracle_mod, grid, b, *outs[0], 1, 300)
+
+
+def test_staged_hit_blocks_equal_direct_loads(ht, oracle_mod):
+    """Hits copied into shared memory in 512-hit blocks (bulk copies) give the
+    accumulators and CSR of direct loads: ragged events (block starts not
+    16-byte aligned, one- to three-hit events with no bulk part, events of
+    many blocks), with and without records, and a misaligned hit array
+    (which falls back to direct loads)."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    parts = [synth.generate(w, n_events=5, first_event=70)]
+    tiny = synth.generate(synth.WORKLOADS["single_event_10trk"], n_events=3)
+    xs = [parts[0].x] + [tiny.x[:k] for k in (1, 3, 2)]
+    ys = [parts[0].y] + [tiny.y[:k] for k in (1, 3, 2)]
+    sizes = list(np.diff(parts[0].event_offsets)) + [1, 3, 2]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    b = synth.from_arrays(np.concatenate(xs), np.concatenate(ys), event_offsets=offs)
+    g = w.grid
+    acc_o = oracle_mod.vote(g, b.x, b.y, b.event_offsets)
+    outs = []
+    for staging, rec in ((1, 1), (0, 1), (1, 0)):
+        opts = ((ht.HT_OPT_HIT_STAGING, staging), (ht.HT_OPT_RECORDS, rec), (ht.HT_OPT_TILE_PHI, 4),
+                (ht.HT_OPT_TILE_D0, 16), (ht.HT_OPT_THREADS, 128))
+        outs.append(_run(ht, g, b, w.threshold, w.window, opts=opts))
+        ctx = ht.Context(g, w.spec.layers)
+        for k, v in opts:
+            ctx.set_option(k, v)
+        assert ctx.get_option(ht.HT_OPT_HIT_STAGING) == staging
+        ctx.vote(ht.Hits.from_batch(b, device="cuda"))
+        for e in range(b.n_events):
+            assert np.array_equal(ctx.accumulator(e), acc_o[e]), (staging, rec, e)
+        ctx.close()
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(a, c)
+    assert np.array_equal(outs[0][0], oracle_mod.peaks(g, acc_o, w.threshold))
+    _check_csr_rows(oracle_mod, g, b, *outs[0], w.window, 300)
+    # hit arrays 4 bytes off a 16-byte boundary: direct loads, same result
+    xb = torch.zeros(b.n_hits + 1, dtype=torch.float32, device="cuda")
+    yb = torch.zeros(b.n_hits + 1, dtype=torch.float32, device="cuda")
+    xb[1:] = torch.from_numpy(b.x).cuda()
+    yb[1:] = torch.from_numpy(b.y).cuda()
+    hits = ht.Hits.from_batch(b, device="cuda")
+    hits.arrays = (xb[1:], yb[1:]) + tuple(hits.arrays[2:])
+    hits.struct.x, hits.struct.y = xb[1:].data_ptr(), yb[1:].data_ptr()
+    ctx = ht.Context(g, w.spec.layers)
+    ctx.set_option(ht.HT_OPT_HIT_STAGING, 1)
+    res = ht.Results(1 << 22, 1 << 27, device="cuda")
+    ctx.process(hits, w.threshold, w.window, res)
+    ctx.sync()
+    for a, c in zip(outs[0], res.host()):
+        assert np.array_equal(a, c)
+    ctx.close()
