@@ -590,8 +590,8 @@ def run_gpu(args):
     waves = ctx.get_option(ht.HT_OPT_WAVES)
     counts = res.counts.cpu().numpy()
     # ---- end to end through the C ABI: pinned host inputs and outputs (measured
-    # right after the device steps, before the reports below allocate); the
-    # same context, so the batch's record memory is held once
+    # right after the device steps, before the reports below allocate), in a
+    # context of its own with the step's tile
     e2e = None
     if not args.no_extras:  # every rank measures its own end-to-end rate
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -608,15 +608,25 @@ def run_gpu(args):
         rh.counts = torch.zeros(2, dtype=torch.int64).pin_memory()
         rh.struct = ht.HtResults(rh.peaks.data_ptr(), rh.peak_cap, rh.peak_offsets.data_ptr(),
                                  rh.hit_idx.data_ptr(), rh.pair_cap, rh.counts.data_ptr(), ht.HT_HOST)
+        ectx = ht.Context(g, w.spec.layers)
+        for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
+                     (ht.HT_OPT_THREADS, tile["threads"]), (ht.HT_OPT_VOTE_ITEMS, ctx.get_option(ht.HT_OPT_VOTE_ITEMS)),
+                     (ht.HT_OPT_HIT_STAGING, ctx.get_option(ht.HT_OPT_HIT_STAGING))):
+            ectx.set_option(k, v)
+        if args.host_chunks:
+            ectx.set_option(ht.HT_OPT_HOST_CHUNKS, args.host_chunks)
         for _ in range(2):  # warm: buffers, first DMA into the pinned pages
-            ctx.process(hits_h, w.threshold, w.window, rh, stream)
+            ectx.process(hits_h, w.threshold, w.window, rh, stream)
         et = []
         for _ in range(max(5, min(args.steps, 9))):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
+            ectx.process(hits_h, w.threshold, w.window, rh, stream)  # synchronous (host outputs)
             et.append(time.perf_counter() - t0)
+        e2e_waves = ectx.get_option(ht.HT_OPT_WAVES)
+        e2e_chunks = ectx.get_option(ht.HT_OPT_HOST_CHUNKS)
+        ectx.close()
         c = rh.counts.numpy()
         h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
         d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
@@ -632,12 +642,9 @@ def run_gpu(args):
         e2e_s = max_over_ranks(float(np.median(et)), world, dev)
         e2e = {"value": world * n_events / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s, "runs_s": et, "stat": "median",
-               "waves": ctx.get_option(ht.HT_OPT_WAVES),
+               "waves": e2e_waves, "host_chunks": e2e_chunks,
                "d2h_gbs": 4.0 * n_copy / (d0.elapsed_time(d1) * 1e-3) / 1e9}
         del rh, hits_h
-        # the device results again for the reports below
-        step()
-        ctx.sync()
 
     # circle fit of the stored candidates of the last step (not in the step)
     fit_ms = []
@@ -696,11 +703,20 @@ def run_gpu(args):
 
     # ---- plain form (one launch sequence per event) on a 512-event sample,
     # median of five timed runs
+    # (its own tile: one event per launch fills the GPU best with other tiles
+    # than the batched step; autotuned on 64 events of the sample)
     plain_ctx = ht.Context(g, w.spec.layers)
-    for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
-                 (ht.HT_OPT_THREADS, tile["threads"]), (ht.HT_OPT_MODE, ht.HT_MODE_PLAIN)):
-        plain_ctx.set_option(k, v)
+    plain_ctx.set_option(ht.HT_OPT_MODE, ht.HT_MODE_PLAIN)
     psub = batch.select(range(0, n_events, 8))
+    if args.tile:
+        for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
+            plain_ctx.set_option(k, int(v))
+    else:
+        plain_ctx.autotune(ht.Hits.from_batch(psub.select(range(0, psub.n_events, 8)), device=dev))
+    plain_tile = {"tile_phi": plain_ctx.get_option(ht.HT_OPT_TILE_PHI),
+                  "tile_d0": plain_ctx.get_option(ht.HT_OPT_TILE_D0),
+                  "threads": plain_ctx.get_option(ht.HT_OPT_THREADS),
+                  "vote_items": plain_ctx.get_option(ht.HT_OPT_VOTE_ITEMS)}
     ph = ht.Hits.from_batch(psub, device=dev)
     pres = ht.Results(int(n_peaks * 0.2) + 4096, int(n_pairs * 0.2) + 65536, device=dev)
     plain_ctx.process(ph, w.threshold, w.window, pres, stream)
@@ -807,6 +823,7 @@ def run_gpu(args):
         "hit_votes_per_s": world * hit_votes / (ms / 1e3),
         "peaks_per_step": int(counts[0]), "pairs_per_step": int(counts[1]),
         "plain_events_per_s": plain_eps, "plain_runs_ms": plain_runs, "plain_stat": "median of 5",
+        "plain_config": {"events": psub.n_events, "sample": "every 8th event of the batch", **plain_tile},
         "batched_over_plain": (n_events / (ms / 1e3)) / plain_eps,
         "phase_ms": {"vote": float(np.mean(vote_ms)), "peaks_assoc": float(np.mean(rest_ms)),
                      "assoc": float(np.mean(assoc_ms))},
@@ -853,6 +870,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed batched steps (no plain form, e2e or CPU baseline); for profiling")
     ap.add_argument("--hit-staging", type=int, default=None, help="HT_OPT_HIT_STAGING (default: the library's)")
+    ap.add_argument("--host-chunks", type=int, default=0, help="HT_OPT_HOST_CHUNKS of the end-to-end pass")
     ap.add_argument("--vote-items", type=int, default=None, help="HT_OPT_VOTE_ITEMS (default: the library's)")
     ap.add_argument("--record-budget-gb", type=float, default=160.0,
                     help="device memory for the vote records (GB); the 4096-event batch needs about 132")

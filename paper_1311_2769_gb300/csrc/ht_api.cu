@@ -46,6 +46,10 @@ struct DBuf {
         p = nullptr;
         n = 0;
     }
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }  // every buffer of a destroyed context is freed, listed below or not
 };
 
 struct GraphKey {
@@ -91,7 +95,7 @@ struct ht_ctx {
     int prune = 3;                   // bit 0: vote, bit 1: association drop hits without a d0 band
     int vote_mode = HT_VOTE_POINT;
     int acap = 0;  // association row cursors per warp (0 = auto)
-    int host_chunks = 16;  // host results: minimum waves, each copied out while the next computes
+    int host_chunks = 4;   // host results: minimum waves, each copied out while the next computes
     int assoc_index = 0;   // 1: point association through the per-layer angular index when hits carry layers
     bool use_index = false;           // the staged batch uses it (set before each step)
     const int8_t* clayer = nullptr;   // layer ids of the staged batch (device)
@@ -1135,6 +1139,8 @@ int ht_destroy(ht_ctx* ctx) {
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaEvent_t ev : ctx->wave_ev) cudaEventDestroy(ev);
     if (ctx->h_wave) cudaFreeHost(ctx->h_wave);
+    ctx->rec.release();
+    ctx->rbits.release();
     ctx->sx.release();
     ctx->sy.release();
     ctx->slayer.release();
@@ -1882,7 +1888,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
                         ctx->threads = thr;
                         ctx->vote_items = items;
                         if (resolve_tiles(ctx) || !ctx->r_rec) continue;
-                        if (plan_waves(ctx, hits, epw, s) || ensure_timing_events(ctx, (int)ctx->wave_start.size() - 1))
+                        if (plan_waves(ctx, hits, ctx->mode == HT_MODE_PLAIN ? 1 : epw, s) || ensure_timing_events(ctx, (int)ctx->wave_start.size() - 1))
                             continue;
                         if (process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s)) continue;  // warm
                         float ms = 1e30f;
@@ -2003,7 +2009,7 @@ int ht_autotune(ht_ctx* ctx, const ht_hits* hits, void* stream) {
                     const bool timing = ctx->timing;
                     if (ensure_timing_events(ctx, 1)) continue;
                     ctx->timing = true;
-                    if (plan_waves(ctx, hits, epw, s)) continue;
+                    if (plan_waves(ctx, hits, ctx->mode == HT_MODE_PLAIN ? 1 : epw, s)) continue;
                     ctx->use_rec = false;  // this loop times the binning association
                     process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s);  // warm
                     process_device(ctx, 9, 1, pk.p, pcap, po.p, hi.p, qcap, s);

@@ -219,3 +219,24 @@ def test_phase_timing_over_waves_and_host_chunks(ht):
         v, r, total, a = ctx.phase_times()
         assert v > 0 and r > 0 and 0 < a <= r and v + r <= total * 1.05
         ctx.close()
+
+
+def test_closing_a_context_frees_its_records(ht):
+    """A context's device memory, records included, is returned on close."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=64, first_event=1000)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ctx = ht.Context(w.grid, synth.LAYERS_13)
+    res = ht.Results(1 << 22, 1 << 26, device="cuda")
+    ctx.process(ht.Hits.from_batch(b, device="cuda"), w.threshold, w.window, res)
+    ctx.sync()
+    assert ctx.get_option(ht.HT_OPT_RECORDS) == 1
+    free1, _ = torch.cuda.mem_get_info()
+    held = free0 - free1
+    assert held > b.n_hits * w.grid.n_phi * w.grid.n_d0  # the records at least
+    ctx.close()
+    del res
+    torch.cuda.empty_cache()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free0 - free2 < 64 << 20, (free0 - free2) / 2 ** 20
