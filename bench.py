@@ -38,12 +38,12 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per hit of one launch on the first 64 events of
 # the batch workload (275,323 hits), from one ncu capture of the kernels as
-# they are now (vote_band_kernel<4, 128, 1> writing records: 0.163314 GB read
-# + 1.321358 GB written; assoc_rec_kernel<4, 2>: 1.713009 + 0.389908 GB); set
-# to None when a kernel changes until it is captured again
+# they are now (vote_band_kernel<4, 128, 1, 0> writing records: 0.164465 GB
+# read + 1.322960 GB written; assoc_rec_kernel<4, 2>: 1.766159 + 0.443076 GB);
+# set to None when a kernel changes until it is captured again
 PROFILE_HITS = 275323
-VOTE_DRAM_PER_HIT = (0.163314 + 1.321358) * 1e9 / PROFILE_HITS
-ASSOC_DRAM_PER_HIT = (1.713009 + 0.389908) * 1e9 / PROFILE_HITS
+VOTE_DRAM_PER_HIT = (0.164465 + 1.322960) * 1e9 / PROFILE_HITS
+ASSOC_DRAM_PER_HIT = (1.766159 + 0.443076) * 1e9 / PROFILE_HITS
 # FP32 lane operations per (hit, phi0, d0) cell of the method: 8 arithmetic
 # (q: 2 products and a difference; a = q - d; den: d^2 and 2dq terms, 3; the
 # kappa scale) + 1 IEEE division + 4 compare/convert (den > 0, w >= 0,
