@@ -142,18 +142,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_single_thread_worker():
-    """--cpu-single-thread: the oracle on one host thread, on the whole
-    single event, the whole dense event and an 8-event subset of the batch
-    (extrapolated per event), plus the flip fraction of the plain float32
-    evaluation against the binary64 bins on a sample of every workload.
-    Prints one JSON line.  Started by the CPU-baseline leg as its own process
-    before any GPU work, so it runs while the GPU is timed."""
+def cpu_single_thread():
+    """The oracle on one host thread, on the whole single event, the whole
+    dense event and a 4-event subset of the batch (extrapolated per event),
+    plus the flip fraction of the plain float32 evaluation against the
+    binary64 bins on a sample of every workload.  Run after every GPU
+    measurement: host work beside the timed end-to-end pass disturbed it."""
     import oracle
     from paper_1311_2769_gb300 import synth
     oracle.build()
     out = {"threads": 1, "events": {}, "flip_fraction_plain_fp32": {}}
-    for name, n in (("single_event_10trk", 1), ("batch_4096_lognormal", 8), ("dense_event_500trk", 1)):
+    for name, n in (("single_event_10trk", 1), ("batch_4096_lognormal", 4), ("dense_event_500trk", 1)):
         w = synth.WORKLOADS[name]
         b = synth.generate(w, n_events=n)
         t0 = time.perf_counter()
@@ -178,32 +177,10 @@ def cpu_single_thread_worker():
         out["flip_fraction_plain_fp32"][name] = {"binary64_votes": v64, "columns_differing": diff,
                                                  "fraction": diff / max(v64, 1), "hits": int(len(x)),
                                                  "sample": "event 0" + (f", {n_hits} random hits" if n_hits else "")}
-    print(json.dumps(out), flush=True)
-    return 0
+    return out
 
 
-def cpu_single_thread_start():
-    """Start the single-thread oracle worker (a fresh process, before the
-    first GPU call)."""
-    try:
-        return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-single-thread"],
-                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, cwd=ROOT)
-    except OSError:
-        return None
-
-
-def cpu_single_thread_finish(proc, timeout=300):
-    if proc is None:
-        return {"error": "not started"}
-    try:
-        out, _ = proc.communicate(timeout=timeout)
-        return json.loads(out.strip().splitlines()[-1])
-    except Exception as e:  # report, do not hide, a failing worker
-        proc.kill()
-        return {"error": f"{type(e).__name__}: {e}"}
-
-
-def cpu_baseline(w, batch, budget_s=15.0, single=None):
+def cpu_baseline(w, batch, budget_s=15.0):
     """The oracle as it stands, event-parallel on every host core (largest
     event first, one event at a time per thread), on a prefix of the
     workload's events whose length is a multiple of the core count and at
@@ -230,8 +207,6 @@ def cpu_baseline(w, batch, budget_s=15.0, single=None):
                      f"vote+peaks+association, one event per thread, largest first", "seconds": dt,
            "hit_votes_per_s": float(sub.n_hits) * w.grid.n_phi * w.grid.n_d0 / dt,
            "all_cores": {"threads": cores, "events": want, "events_per_s": want / dt}}
-    if single is not None:
-        out["single_thread"] = single
     return out
 
 
@@ -494,9 +469,6 @@ def run_gpu(args):
     import torch.distributed as dist
 
     rank, world, local = _dist()
-    single_proc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
-        single_proc = cpu_single_thread_start()  # its own process, before the first GPU call
 
     from paper_1311_2769_gb300 import build, ht, synth
 
@@ -804,7 +776,16 @@ def run_gpu(args):
     ceilings = vote_ceilings(ht, g, batch, w, hit_votes, vote_s, vote_traffic * launches_per if vote_traffic else None,
                              peaks, dev) if rank == 0 else None
     acc_bytes = 4.0 * g.n_phi * g.n_d0 * g.n_kappa * n_events
-    single = cpu_single_thread_finish(single_proc) if single_proc is not None else None
+    # the CPU leg after every GPU measurement: all cores, then one thread
+    cpu = None
+    single = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, batch)
+        try:
+            single = cpu_single_thread()
+        except Exception as e:  # report, do not hide, a failing measurement
+            single = {"error": f"{type(e).__name__}: {e}"}
+        cpu["single_thread"] = single
     flips = None
     if single and "flip_fraction_plain_fp32" in single:
         flips = {"binary64_definition_gpu": 0.0,
@@ -844,8 +825,8 @@ def run_gpu(args):
         "merge": merge_info,
         "vertex": vertex,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, batch, single=single)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -874,10 +855,7 @@ def main():
     ap.add_argument("--vote-items", type=int, default=None, help="HT_OPT_VOTE_ITEMS (default: the library's)")
     ap.add_argument("--record-budget-gb", type=float, default=160.0,
                     help="device memory for the vote records (GB); the 4096-event batch needs about 132")
-    ap.add_argument("--cpu-single-thread", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.cpu_single_thread:
-        return cpu_single_thread_worker()
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
