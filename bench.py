@@ -498,6 +498,8 @@ def run_gpu(args):
         ctx.set_option(ht.HT_OPT_HIT_STAGING, args.hit_staging)
     if args.vote_items is not None:
         ctx.set_option(ht.HT_OPT_VOTE_ITEMS, args.vote_items)
+    if args.band_split is not None:
+        ctx.set_option(ht.HT_OPT_BAND_SPLIT, args.band_split)
     if args.tile:
         for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
             ctx.set_option(k, int(v))
@@ -514,6 +516,7 @@ def run_gpu(args):
             ctx.autotune(ht.Hits.from_batch(sample, device=dev))
     tile = {"tile_phi": ctx.get_option(ht.HT_OPT_TILE_PHI), "tile_d0": ctx.get_option(ht.HT_OPT_TILE_D0),
             "threads": ctx.get_option(ht.HT_OPT_THREADS)}
+    band_split = ctx.get_option(ht.HT_OPT_BAND_SPLIT)
 
     # size outputs from one untimed pass
     probe = ht.Results(1 << 20, 1 << 20, device=dev)
@@ -583,7 +586,8 @@ def run_gpu(args):
         ectx = ht.Context(g, w.spec.layers)
         for k, v in ((ht.HT_OPT_TILE_PHI, tile["tile_phi"]), (ht.HT_OPT_TILE_D0, tile["tile_d0"]),
                      (ht.HT_OPT_THREADS, tile["threads"]), (ht.HT_OPT_VOTE_ITEMS, ctx.get_option(ht.HT_OPT_VOTE_ITEMS)),
-                     (ht.HT_OPT_HIT_STAGING, ctx.get_option(ht.HT_OPT_HIT_STAGING))):
+                     (ht.HT_OPT_HIT_STAGING, ctx.get_option(ht.HT_OPT_HIT_STAGING)),
+                     (ht.HT_OPT_BAND_SPLIT, ctx.get_option(ht.HT_OPT_BAND_SPLIT))):
             ectx.set_option(k, v)
         if args.host_chunks:
             ectx.set_option(ht.HT_OPT_HOST_CHUNKS, args.host_chunks)
@@ -670,7 +674,8 @@ def run_gpu(args):
                               "events": n_events, "phase_ms": {"vote": float(np.mean(vote_ms)),
                                                                "peaks_assoc": float(np.mean(rest_ms)),
                                                                "assoc": float(np.mean(assoc_ms))},
-                              "peaks": int(counts[0]), "pairs": int(counts[1]), "tile": tile}), flush=True)
+                              "peaks": int(counts[0]), "pairs": int(counts[1]), "tile": tile,
+                              "band_split": band_split}), flush=True)
         return 0
 
     # ---- plain form (one launch sequence per event) on a 512-event sample,
@@ -679,6 +684,8 @@ def run_gpu(args):
     # than the batched step; autotuned on 64 events of the sample)
     plain_ctx = ht.Context(g, w.spec.layers)
     plain_ctx.set_option(ht.HT_OPT_MODE, ht.HT_MODE_PLAIN)
+    if args.band_split is not None:
+        plain_ctx.set_option(ht.HT_OPT_BAND_SPLIT, args.band_split)
     psub = batch.select(range(0, n_events, 8))
     if args.tile:
         for k, v in zip((ht.HT_OPT_TILE_PHI, ht.HT_OPT_TILE_D0, ht.HT_OPT_THREADS), args.tile.split(",")):
@@ -800,7 +807,7 @@ def run_gpu(args):
                    "grid": [g.n_phi, g.n_d0, g.n_kappa], "threshold": w.threshold, "window": w.window,
                    "mode": "batched persistent + CUDA graph", "l2": "flushed between timed steps",
                    "parallelism": f"events sharded, {world} independent rank(s)", "waves": waves,
-                   "records": records, **tile},
+                   "records": records, "band_split": band_split, **tile},
         "hit_votes_per_s": world * hit_votes / (ms / 1e3),
         "peaks_per_step": int(counts[0]), "pairs_per_step": int(counts[1]),
         "plain_events_per_s": plain_eps, "plain_runs_ms": plain_runs, "plain_stat": "median of 5",
@@ -853,6 +860,7 @@ def main():
     ap.add_argument("--hit-staging", type=int, default=None, help="HT_OPT_HIT_STAGING (default: the library's)")
     ap.add_argument("--host-chunks", type=int, default=0, help="HT_OPT_HOST_CHUNKS of the end-to-end pass")
     ap.add_argument("--vote-items", type=int, default=None, help="HT_OPT_VOTE_ITEMS (default: the library's)")
+    ap.add_argument("--band-split", type=int, default=None, help="HT_OPT_BAND_SPLIT (default: the library's)")
     ap.add_argument("--record-budget-gb", type=float, default=160.0,
                     help="device memory for the vote records (GB); the 4096-event batch needs about 132")
     args = ap.parse_args()

@@ -166,6 +166,12 @@ typedef struct {
                                       double-buffered, instead of loading them per warp; used when x
                                       and y are 16-byte aligned.  A copy that never completes (a bounded
                                       wait) is reported as HT_ERR_TIMEOUT.  Default 0; same results. */
+#define HT_OPT_BAND_SPLIT 22      /* hull band vote (HT_OPT_VOTE_ITEMS 0, hits loaded per warp): hits
+                                      whose d0 band spans at most this many of the tile's columns are
+                                      queued apart from the rest, and each of them walks its own band
+                                      instead of the hull of 32 hits' bands; 0: one queue for all.
+                                      -1 (default): tile_d0 * 5 / 16, at least 3.  Reads back the value
+                                      in use.  Same accumulators and records either way. */
 #define HT_OPT_WAVES 19            /* read-only: waves (kernel sequences over groups of events) of the
                                       last ht_process */
 #define HT_OPT_RECORD_BUDGET 18    /* device memory for those records in bytes (0 = 72 GB): a wave of

@@ -122,6 +122,8 @@ struct ht_ctx {
     int r_rec_variant = 3;                 // the record-writing vote kernel
     int vote_items = 0;                    // band vote over (hit, column) items (1) or the hull of queued hits (0)
     int hit_staging = 0;                   // hull band vote: hits staged into shared memory by bulk copies
+    int band_split = -1;                   // hull band vote: narrow-band queue threshold (-1 auto, 0 off)
+    int r_narrow = 0;                      // resolved threshold passed to the kernel
     bool r_stage = false;                  // staged variants prepared for the resolved tile
     int r_stage_blocks_per_sm = 1, r_stage_rec_blocks_per_sm = 1, r_stage_smem = 0;
     int rc_threads = 128, rc_cap = 256, rc_blocks_per_sm = 1;
@@ -350,7 +352,8 @@ int resolve_tiles(ht_ctx* ctx) {
     const bool line = ctx->vote_mode == HT_VOTE_LINE;
     const bool range = ctx->vote_mode == HT_VOTE_RANGE || line;
     // bands bound point votes only: range and line voting sweep every cell
-    const bool band = !range && (ctx->prune & 1) && ctx->K.band_ok;
+    // queued bands keep their ends in one byte each: tiles of at most 256 columns
+    const bool band = !range && (ctx->prune & 1) && ctx->K.band_ok && td <= 256;
     ctx->a_band = !range && (ctx->prune & 2) && ctx->K.band_ok;
     const int variant = ctx->vote_mode == HT_VOTE_RANGE ? 2 : (band ? (ctx->vote_items ? 4 : 1) : 0);
     const int smem = vote_smem_bytes(tp, td, nk, thr, variant);
@@ -361,6 +364,7 @@ int resolve_tiles(ht_ctx* ctx) {
     CU(vote_occupancy(tp, nk, thr, smem, &per_sm, variant));
     ctx->r_band = band;
     ctx->r_variant = variant;
+    ctx->r_narrow = variant == 1 ? (ctx->band_split >= 0 ? ctx->band_split : std::max(3, td * 5 / 16)) : 0;
     if (per_sm < 1) return fail(ctx, HT_ERR_INVALID_ARG, "vote tile %dx%dx%d with %d threads cannot launch", tp, td, nk, thr);
     ctx->r_tile_phi = tp;
     ctx->r_tile_d = td;
@@ -627,6 +631,7 @@ VoteParams vote_params(ht_ctx* ctx, int32_t event0, int32_t ne, bool persistent)
     p.K = ctx->K;
     p.stats = ctx->count_stages ? ctx->d_stats : nullptr;
     p.err = ctx->d_err;
+    p.narrow = ctx->r_narrow;
     return p;
 }
 
@@ -1242,6 +1247,10 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "hit staging must be 0 or 1");
             ctx->hit_staging = (int)value;
             break;
+        case HT_OPT_BAND_SPLIT:
+            if (value < -1 || value > 256) return fail(ctx, HT_ERR_INVALID_ARG, "band split must be in [-1, 256]");
+            ctx->band_split = (int)value;
+            break;
         case HT_OPT_RECORD_BUDGET:
             if (value < 0) return fail(ctx, HT_ERR_INVALID_ARG, "record budget < 0");
             ctx->rec_budget = value ? value : kDefaultRecBudget;
@@ -1277,7 +1286,7 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
     ctx->gvalid = false;
     if (key == HT_OPT_TILE_PHI || key == HT_OPT_TILE_D0 || key == HT_OPT_THREADS || key == HT_OPT_ATILE_PHI ||
         key == HT_OPT_ATILE_D0 || key == HT_OPT_PRUNE || key == HT_OPT_VOTE_MODE || key == HT_OPT_ASSOC_CURSORS ||
-        key == HT_OPT_RECORDS || key == HT_OPT_VOTE_ITEMS || key == HT_OPT_HIT_STAGING) {
+        key == HT_OPT_RECORDS || key == HT_OPT_VOTE_ITEMS || key == HT_OPT_HIT_STAGING || key == HT_OPT_BAND_SPLIT) {
         int st = resolve_tiles(ctx);
         if (st) return st;
     }
@@ -1306,6 +1315,7 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_RECORDS: *value = ctx->r_rec ? 1 : 0; break;
         case HT_OPT_VOTE_ITEMS: *value = ctx->vote_items; break;
         case HT_OPT_HIT_STAGING: *value = ctx->r_stage ? 1 : 0; break;
+        case HT_OPT_BAND_SPLIT: *value = ctx->r_narrow; break;
         case HT_OPT_RECORD_BUDGET: *value = ctx->rec_budget; break;
         case HT_OPT_WAVES: *value = ctx->wave_start.empty() ? 0 : (int64_t)ctx->wave_start.size() - 1; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);

@@ -41,6 +41,7 @@ struct VoteParams {
     uint32_t* rbits;
     int32_t rec_bytes;
     int32_t* err;          // staged hit loads: bit 16 when a block copy did not complete
+    int32_t narrow;        // band vote: bands of at most this many columns walk their own band (0: none)
 };
 
 struct PeakParams {

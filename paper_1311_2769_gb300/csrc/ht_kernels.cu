@@ -198,6 +198,73 @@ __device__ __forceinline__ void vote_xy_rec(const VoteParams& p, const float* cp
     }
 }
 
+// vote_xy (TAIL form), optionally writing the hit's record, with each lane
+// walking its own band [lo, hi] from its first column: step s evaluates
+// column lo + s, so `steps` (the widest band of the warp) replaces the hull
+// of the warp's bands.  Lanes past their band idle.  With REC the whole
+// record is first set to 255 (16-byte stores), then the band's columns are
+// written.  Idle and invalid lanes have lo in range (the dt load stays
+// inside the tile table) and hi < lo.
+template <int SPHI, int NK, bool REC>
+__device__ __forceinline__ void vote_xy_al(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
+                                           uint32_t* acc_s, uint32_t acc_sh, int lo, int hi, int steps, int nk,
+                                           float x, float y, bool valid, uint8_t* rec) {
+    using W = typename RecWord<SPHI>::T;
+    const HitFast hf = hit_fast(x, y, p.K);
+    const float S2 = p.K.S2, H = p.K.H, T0 = p.K.T0;
+    float q[SPHI], qs[SPHI];
+#pragma unroll
+    for (int r = 0; r < SPHI; ++r) {
+        q[r] = q_of(x, y, cp[r], sp[r]);
+        qs[r] = q[r] * S2;
+    }
+    const unsigned nku = (unsigned)nk;
+    const int col_words = SPHI * nk;
+    W* rw = reinterpret_cast<W*>(rec);
+    if (REC && valid) {
+        uint4* r4 = reinterpret_cast<uint4*>(rec);
+        const uint4 none = make_uint4(~0u, ~0u, ~0u, ~0u);
+        for (int b = 0; b < (p.rec_bytes >> 4); ++b) r4[b] = none;
+    }
+    for (int s = 0; s < steps; ++s) {
+        const int j = lo + s;
+        const bool act = valid & (j <= hi);
+        const int jc = act ? j : lo;
+        const float4 dt = dt_s[jc];
+        const float Rj = hf.r2 + dt.z;
+        const uint32_t col_sh = acc_sh + 4u * (unsigned)(jc * col_words);
+        bool und = false;
+        uint32_t wlo = 0, whi = 0;
+#pragma unroll
+        for (int r = 0; r < SPHI; ++r) {
+            const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+            const uint32_t addr = col_sh + 4u * ((unsigned)(r * nk) + o.kb);
+            if (REC) {
+                if (r < 4)
+                    wlo = red_and_byte(addr, o.flo, o.fhi, o.kb, nku, act, wlo, 8u * r);
+                else
+                    whi = red_and_byte(addr, o.flo, o.fhi, o.kb, nku, act, whi, 8u * (r - 4));
+            } else {
+                red_if_vote(addr, o.flo, o.fhi, o.kb, nku, act);
+            }
+            und |= (o.flo != o.fhi) & act;
+        }
+        W word = (W)(SPHI == 8 ? ((unsigned long long)whi << 32) | wlo : wlo);
+        if (__any_sync(0xffffffffu, und)) {
+#pragma unroll
+            for (int r = 0; r < SPHI; ++r) {
+                const S1 o = stage1_fast(qs[r], q[r], dt, Rj, hf.G, H, T0);
+                if ((o.flo != o.fhi) && act && stage1_pending(o, hf.dmin, p.K.wlo, p.K.whi)) {
+                    const int kk = cell_slow(x, y, cp[r], sp[r], dt.x, hf.R1, p.K, p.stats);
+                    if (kk >= 0) atomicAdd(acc_s + jc * col_words + r * nk + kk, 1u);
+                    if (REC) word = (word & ~((W)0xFF << (8 * r))) | ((W)(kk >= 0 ? (unsigned)kk : 255u) << (8 * r));
+                }
+            }
+        }
+        if (REC && act) rw[j] = word;
+    }
+}
+
 template <int SPHI, int NK>
 __device__ __forceinline__ void vote_one_hit_rec(const VoteParams& p, const float* cp, const float* sp,
                                                  const float4* dt_s, uint32_t* acc_s, uint32_t acc_sh, int ja, int jb,
@@ -393,21 +460,47 @@ __device__ __forceinline__ void vote_queued_xy(const VoteParams& p, const float*
         vote_xy<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid);
 }
 
-template <int SPHI, int NK, bool REC>
-__device__ __forceinline__ void vote_queued(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
-                                            uint32_t* acc_s, uint32_t acc_sh, const uint2* hq, unsigned head, int n,
-                                            int nj, int nk, int lane, uint8_t* rec_t, int64_t hb) {
+// Per-warp band queues of the directly loaded band vote: two rings of
+// kHitQueue entries, ring 0 the narrow bands (at most p.narrow columns),
+// ring 1 the rest.  An entry is the hit's offset in its event and its band
+// (lo | hi << 8, tile columns).
+struct BandRings {
+    uint32_t* off;   // [2][kHitQueue]
+    uint16_t* band;  // [2][kHitQueue]
+};
+
+__host__ __device__ constexpr int band_ring_bytes() { return 2 * kHitQueue * 6; }
+
+// One batch of up to 32 queued hits: lanes [0, n0) take ring c0 from head
+// h0, lanes [n0, n0 + n1) ring 1 from head h1.  ALIGNED: each lane walks its
+// own band (narrow or mixed batches); otherwise the hull of the bands.
+template <int SPHI, int NK, bool REC, bool ALIGNED>
+__device__ __forceinline__ void vote_batch(const VoteParams& p, const float* cp, const float* sp, const float4* dt_s,
+                                           uint32_t* acc_s, uint32_t acc_sh, const BandRings& q, int c0, unsigned h0,
+                                           int n0, unsigned h1, int n1, int nj, int nk, int lane, uint8_t* rec_t,
+                                           int64_t hb) {
     __syncwarp();
-    const bool valid = lane < n;
-    const uint2 ent = valid ? hq[(head + lane) & (kHitQueue - 1)] : make_uint2(0u, 0u);
-    const int lo = valid ? (int)(ent.y & 0xFFFFu) : nj, hi = valid ? (int)(ent.y >> 16) : -1;
-    const int ja = __reduce_min_sync(0xffffffffu, lo), jb = __reduce_max_sync(0xffffffffu, hi);
+    const bool valid = lane < n0 + n1;
+    const int slot = lane < n0 ? c0 * kHitQueue + (int)((h0 + lane) & (kHitQueue - 1))
+                               : kHitQueue + (int)((h1 + (lane - n0)) & (kHitQueue - 1));
+    const uint32_t off = valid ? q.off[slot] : 0u;
+    const unsigned bd = valid ? q.band[slot] : 0u;
     __syncwarp();  // entries read before their slots are reused
-    if (REC)
-        vote_one_hit_rec<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid,
-                                   rec_t + ((int64_t)ent.x - hb) * p.rec_bytes);
-    else
-        vote_one_hit<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, (int64_t)ent.x, valid);
+    const float x = valid ? p.x[hb + off] : 0.0f;
+    const float y = valid ? p.y[hb + off] : 0.0f;
+    uint8_t* rec = REC ? rec_t + (int64_t)off * p.rec_bytes : nullptr;
+    if (ALIGNED) {
+        const int lo = valid ? (int)(bd & 0xFFu) : 0, hi = valid ? (int)(bd >> 8) : -1;
+        const int steps = __reduce_max_sync(0xffffffffu, (unsigned)(hi - lo + 1));
+        vote_xy_al<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, lo, hi, steps, nk, x, y, valid, rec);
+    } else {
+        const int lo = valid ? (int)(bd & 0xFFu) : nj, hi = valid ? (int)(bd >> 8) : -1;
+        const int ja = __reduce_min_sync(0xffffffffu, lo), jb = __reduce_max_sync(0xffffffffu, hi);
+        if (REC)
+            vote_xy_rec<SPHI, NK>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid, rec);
+        else
+            vote_xy<SPHI, NK, true>(p, cp, sp, dt_s, acc_s, acc_sh, ja, jb, nk, x, y, valid);
+    }
 }
 
 template <int SPHI, int NK, bool REC, bool STAGE>
@@ -416,12 +509,15 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
     float4* dt_s = reinterpret_cast<float4*>(smem_raw);
     const int nthr = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-    constexpr int QB = STAGE ? 16 : 8;  // queue entry: (hit, band) [+ x, y when staged]
-    uint2* hq = reinterpret_cast<uint2*>(smem_raw + 16 * p.tile_d) + warp * kHitQueue;
+    // queues: staged, one ring of (hit, band, x, y); direct, two band rings
+    const int qbytes = STAGE ? 16 * kHitQueue : band_ring_bytes();
     uint4* hq4 = reinterpret_cast<uint4*>(smem_raw + 16 * p.tile_d) + warp * kHitQueue;
-    float* stg = reinterpret_cast<float*>(smem_raw + 16 * p.tile_d + QB * kHitQueue * nw);
+    BandRings rings;
+    rings.off = reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d) + warp * 2 * kHitQueue;
+    rings.band = reinterpret_cast<uint16_t*>(smem_raw + 16 * p.tile_d + 8 * kHitQueue * nw) + warp * 2 * kHitQueue;
+    float* stg = reinterpret_cast<float*>(smem_raw + 16 * p.tile_d + qbytes * nw);
     uint32_t* acc_s =
-        reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d + QB * kHitQueue * nw + (STAGE ? kStageBytes : 0));
+        reinterpret_cast<uint32_t*>(smem_raw + 16 * p.tile_d + qbytes * nw + (STAGE ? kStageBytes : 0));
     __shared__ int s_item;
     __shared__ __align__(8) uint64_t s_bar[2];
     unsigned par[2] = {0u, 0u};
@@ -491,7 +587,8 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
             rec_t = p.rec + ((hb - whb) * tiles + (int64_t)t * (he - hb)) * p.rec_bytes;
             bits_t = p.rbits + (((hb - whb) >> 5) + e) * (int64_t)tiles + (int64_t)t * ((he - hb + 31) >> 5);
         }
-        unsigned head = 0, tail = 0;
+        unsigned head = 0, tail = 0;     // staged ring; direct: the wide ring
+        unsigned nhead = 0, ntail = 0;   // direct: the narrow ring
         // one chunk of 32 hits: bands, the bitmap word, queueing and votes
         auto chunk = [&](int64_t c0, int64_t cend, const float* xs, const float* ys, int64_t base) {
             const int64_t h = c0 + lane;
@@ -512,21 +609,37 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
             const bool keep = valid && hi >= lo;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (REC && lane == 0) bits_t[(c0 - hb) >> 5] = m;
-            const unsigned slot = (tail + __popc(m & lt)) & (kHitQueue - 1);
-            const unsigned band = (unsigned)lo | ((unsigned)hi << 16);
-            if (keep) {
-                if (STAGE)
-                    hq4[slot] = make_uint4((unsigned)h, band, __float_as_uint(x), __float_as_uint(y));
-                else
-                    hq[slot] = make_uint2((unsigned)h, band);
-            }
-            tail += __popc(m);
-            if (tail - head >= 32) {
-                if (STAGE)
+            if (STAGE) {
+                const unsigned slot = (tail + __popc(m & lt)) & (kHitQueue - 1);
+                const unsigned band = (unsigned)lo | ((unsigned)hi << 16);
+                if (keep) hq4[slot] = make_uint4((unsigned)h, band, __float_as_uint(x), __float_as_uint(y));
+                tail += __popc(m);
+                if (tail - head >= 32) {
                     vote_queued_xy<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq4, head, 32, nj, nk, lane, rec_t, hb);
-                else
-                    vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, 32, nj, nk, lane, rec_t, hb);
-                head += 32;
+                    head += 32;
+                }
+            } else {
+                const bool nar = keep && hi - lo < p.narrow;
+                const unsigned mn = __ballot_sync(0xffffffffu, nar);
+                const unsigned mw = m & ~mn;
+                if (keep) {
+                    const int slot = nar ? (int)((ntail + __popc(mn & lt)) & (kHitQueue - 1))
+                                         : kHitQueue + (int)((tail + __popc(mw & lt)) & (kHitQueue - 1));
+                    rings.off[slot] = (uint32_t)(h - hb);
+                    rings.band[slot] = (uint16_t)(lo | (hi << 8));
+                }
+                ntail += __popc(mn);
+                tail += __popc(mw);
+                if (tail - head >= 32) {
+                    vote_batch<SPHI, NK, REC, false>(p, cp, sp, dt_s, acc_s, acc_sh, rings, 1, head, 32, 0u, 0, nj, nk,
+                                                     lane, rec_t, hb);
+                    head += 32;
+                }
+                if (ntail - nhead >= 32) {
+                    vote_batch<SPHI, NK, REC, true>(p, cp, sp, dt_s, acc_s, acc_sh, rings, 0, nhead, 32, 0u, 0, nj, nk,
+                                                    lane, rec_t, hb);
+                    nhead += 32;
+                }
             }
         };
         if (!STAGE) {
@@ -573,13 +686,24 @@ __global__ void __launch_bounds__(256, 3) vote_band_kernel(const VoteParams p) {
                 if (tid == 0 && b + 2 < nblk) stage_issue(p, stg, s_bar, hb, he, b + 2);
             }
         }
-        if (tail != head) {
-            if (STAGE)
+        if (STAGE) {
+            if (tail != head)
                 vote_queued_xy<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq4, head, (int)(tail - head), nj, nk, lane,
                                               rec_t, hb);
-            else
-                vote_queued<SPHI, NK, REC>(p, cp, sp, dt_s, acc_s, acc_sh, hq, head, (int)(tail - head), nj, nk, lane,
-                                           rec_t, hb);
+        } else {
+            // the rings' remainders: one batch walking each lane's own band
+            // when they fit in 32 lanes together, else one batch each
+            const int nn = (int)(ntail - nhead), nw2 = (int)(tail - head);
+            if (nn + nw2 <= 32) {
+                if (nn + nw2 > 0)
+                    vote_batch<SPHI, NK, REC, true>(p, cp, sp, dt_s, acc_s, acc_sh, rings, 0, nhead, nn, head, nw2, nj,
+                                                    nk, lane, rec_t, hb);
+            } else {
+                vote_batch<SPHI, NK, REC, true>(p, cp, sp, dt_s, acc_s, acc_sh, rings, 0, nhead, nn, 0u, 0, nj, nk, lane,
+                                                rec_t, hb);
+                vote_batch<SPHI, NK, REC, false>(p, cp, sp, dt_s, acc_s, acc_sh, rings, 1, head, nw2, 0u, 0, nj, nk,
+                                                 lane, rec_t, hb);
+            }
         }
         __syncthreads();
 
@@ -2184,7 +2308,7 @@ __global__ void rcp_check_kernel(uint32_t first_bits, uint32_t count, unsigned l
 // ---------------------------------------------------------------------------
 int vote_smem_bytes(int tile_phi, int tile_d, int nk, int threads, int variant) {
     const int warps = threads / 32;
-    int queues = variant == 1 || variant == 3 ? warps * kHitQueue * 8 : 0;
+    int queues = variant == 1 || variant == 3 ? warps * band_ring_bytes() : 0;
     if (variant == 6 || variant == 7) queues = warps * kHitQueue * 16 + kStageBytes;
     // item vote: a slot per lane and an item map of 32 * tile_d bytes per warp
     if (variant == 4 || variant == 5) queues = warps * 32 * flat_slot_bytes(tile_phi) + ((32 * tile_d * warps + 15) & ~15);

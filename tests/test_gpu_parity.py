@@ -578,3 +578,51 @@ def test_staged_hit_blocks_equal_direct_loads(ht, oracle_mod):
     for a, c in zip(outs[0], res.host()):
         assert np.array_equal(a, c)
     ctx.close()
+
+
+def test_band_split_equals_oracle(ht, oracle_mod):
+    """Narrow-band hits queued apart and walking their own bands give the
+    accumulators, records, peaks and rows of one hull queue and of the
+    oracle: splits 0 (one queue), auto, 3, every band narrow (16, 256), with
+    and without records, 4 x 16 and 8 x 8 tiles, a ragged 4 x 12 tile, and
+    events of one to three hits (partial rings merged into one batch)."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    part = synth.generate(w, n_events=4, first_event=90)
+    tiny = synth.generate(synth.WORKLOADS["single_event_10trk"], n_events=3)
+    xs = [part.x] + [tiny.x[:k] for k in (1, 3, 2)]
+    ys = [part.y] + [tiny.y[:k] for k in (1, 3, 2)]
+    sizes = list(np.diff(part.event_offsets)) + [1, 3, 2]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    b = synth.from_arrays(np.concatenate(xs), np.concatenate(ys), event_offsets=offs)
+    g = w.grid
+    acc_o = oracle_mod.vote(g, b.x, b.y, b.event_offsets)
+    ref = None
+    for tp, td in ((4, 16), (8, 8), (4, 12)):
+        for split in (0, -1, 3, 16, 256):
+            for rec in (1, 0):
+                if rec == 0 and split not in (0, -1):
+                    continue
+                opts = ((ht.HT_OPT_BAND_SPLIT, split), (ht.HT_OPT_RECORDS, rec), (ht.HT_OPT_TILE_PHI, tp),
+                        (ht.HT_OPT_TILE_D0, td), (ht.HT_OPT_THREADS, 128))
+                out = _run(ht, g, b, w.threshold, w.window, opts=opts)
+                if ref is None:
+                    ref = out
+                else:
+                    for a, c in zip(ref, out):
+                        assert np.array_equal(a, c), (tp, td, split, rec)
+                ctx = ht.Context(g, w.spec.layers)
+                for k, v in opts:
+                    ctx.set_option(k, v)
+                want = {0: 0, -1: max(3, td * 5 // 16)}.get(split, split)
+                assert ctx.get_option(ht.HT_OPT_BAND_SPLIT) == want
+                ctx.vote(ht.Hits.from_batch(b, device="cuda"))
+                for e in range(b.n_events):
+                    assert np.array_equal(ctx.accumulator(e), acc_o[e]), (tp, td, split, rec, e)
+                ctx.close()
+    assert np.array_equal(ref[0], oracle_mod.peaks(g, acc_o, w.threshold))
+    _check_csr_rows(oracle_mod, g, b, *ref, w.window, 300)
+    # the option's range
+    ctx = ht.Context(g, w.spec.layers)
+    with pytest.raises(ht.HtError):
+        ctx.set_option(ht.HT_OPT_BAND_SPLIT, -2)
+    ctx.close()
