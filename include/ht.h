@@ -144,7 +144,7 @@ typedef struct {
                                       cursors.  Reading gives the resolved value. */
 #define HT_OPT_HOST_CHUNKS 15      /* ht_process with host results (batched mode): run the batch in at
                                       least this many waves and copy each wave's peaks and CSR to the
-                                      host while later waves compute (1..64, default 4; 1 = copy after
+                                      host while later waves compute (1..64, default 8; 1 = copy after
                                       the whole batch) */
 #define HT_OPT_ASSOC_INDEX 16      /* 1: ht_process associates point votes through a per-(event,
                                       layer) index of hit angles, binning only the hits whose exact

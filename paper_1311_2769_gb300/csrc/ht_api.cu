@@ -95,7 +95,7 @@ struct ht_ctx {
     int prune = 3;                   // bit 0: vote, bit 1: association drop hits without a d0 band
     int vote_mode = HT_VOTE_POINT;
     int acap = 0;  // association row cursors per warp (0 = auto)
-    int host_chunks = 4;   // host results: minimum waves, each copied out while the next computes
+    int host_chunks = 8;   // host results: minimum waves, each copied out while the next computes
     int assoc_index = 0;   // 1: point association through the per-layer angular index when hits carry layers
     bool use_index = false;           // the staged batch uses it (set before each step)
     const int8_t* clayer = nullptr;   // layer ids of the staged batch (device)
@@ -184,7 +184,8 @@ struct ht_ctx {
     // (pinned, written by the step), an event after each wave, a copy stream
     bool wave_marks = false;
     std::vector<cudaEvent_t> wave_ev;
-    int64_t* h_wave = nullptr;
+    int64_t* h_wave = nullptr;      // pinned, mapped: per-wave running totals written by publish_kernel
+    int64_t* d_h_wave = nullptr;    // its device address
     int h_wave_n = 0;
     cudaStream_t copy_stream = nullptr;
     bool pending_check = false;
@@ -1000,10 +1001,11 @@ int process_device(ht_ctx* ctx, uint32_t thr, int32_t window, ht_peak* peaks, in
         if (st) return st;
         if ((st = mark(ctx, wi, 2, s))) return st;
         if (ctx->wave_marks) {  // running totals after this wave, then its event (host copies follow it)
-            CU(cudaMemcpyAsync(ctx->h_wave + 2 * wi, ctx->d_scal, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CU(launch_publish(ctx->d_scal, ctx->d_h_wave + 2 * wi, s));
             CU(cudaEventRecord(ctx->wave_ev[wi], s));
         }
-        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode != HT_VOTE_POINT ? 1 : 0);
+        ctx->launches += (plain ? 1 : 2) + 1 + 3 + 1 + 3 + 1 + (ctx->vote_mode != HT_VOTE_POINT ? 1 : 0) +
+                         (ctx->wave_marks ? 1 : 0);
     }
     if (nwaves > 0 && (st = mark(ctx, nwaves - 1, 3, s))) return st;
     if (ctx->c_events == 0 && peak_offsets && peak_cap >= 0)
@@ -1495,8 +1497,11 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         if (ctx->h_wave_n < nwaves) {
             if (ctx->h_wave) cudaFreeHost(ctx->h_wave);
             ctx->h_wave = nullptr;
+            ctx->d_h_wave = nullptr;
             ctx->h_wave_n = 0;
-            CU(cudaMallocHost(&ctx->h_wave, 2 * sizeof(int64_t) * (size_t)nwaves));
+            CU(cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_wave), 2 * sizeof(int64_t) * (size_t)nwaves,
+                             cudaHostAllocMapped));
+            CU(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_h_wave), ctx->h_wave, 0));
             ctx->h_wave_n = nwaves;
         }
         if (!ctx->copy_stream) CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));

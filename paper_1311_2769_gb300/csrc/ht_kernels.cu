@@ -2280,6 +2280,16 @@ __global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p
 }
 
 // counts[0..1] = {peaks, pairs of stored peaks + pairs of peaks beyond the cap}
+// The running totals after a wave, stored straight into pinned host memory
+// (device-accessible under unified addressing).  A 16-byte copy-engine copy
+// on the compute stream would wait behind the copy stream's result copies,
+// which share the device-to-host engine, and stall the next wave.
+__global__ void publish_kernel(const int64_t* scal, int64_t* host) {
+    host[0] = scal[0];
+    host[1] = scal[1];
+    __threadfence_system();
+}
+
 __global__ void finalize_kernel(int64_t* scal) {
     scal[6] = scal[0];
     scal[7] = scal[1] + scal[4];
@@ -2455,6 +2465,11 @@ cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blo
     void* f = vote_variant(tile_phi, nk, variant);
     if (!f) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
+}
+
+cudaError_t launch_publish(const int64_t* scal, int64_t* host, cudaStream_t s) {
+    publish_kernel<<<1, 1, 0, s>>>(scal, host);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int64_t* scal, cudaStream_t s) {
