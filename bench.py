@@ -602,12 +602,13 @@ def run_gpu(args):
             et.append(time.perf_counter() - t0)
         e2e_waves = ectx.get_option(ht.HT_OPT_WAVES)
         e2e_chunks = ectx.get_option(ht.HT_OPT_HOST_CHUNKS)
+        e2e_copy = ectx.get_option(ht.HT_OPT_HOST_COPY)
         ectx.close()
         c = rh.counts.numpy()
         h2d = n_hits * (4 + 4 + 1) + 4 * (n_events + 1)
         d2h = 16 + int(c[0]) * 20 + (int(c[0]) + 1) * 8 + int(c[1]) * 4
-        # the box's pinned device-to-host copy rate (1 GiB into the result
-        # buffer), which bounds this number once the copies overlap compute
+        # the box's pinned device-to-host copy-engine rate (1 GiB into the
+        # result buffer; the library's copy kernel does not use the engines)
         n_copy = min(1 << 28, rh.pair_cap)
         d0 = torch.cuda.Event(enable_timing=True)
         d1 = torch.cuda.Event(enable_timing=True)
@@ -619,6 +620,7 @@ def run_gpu(args):
         e2e = {"value": world * n_events / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s, "runs_s": et, "stat": "median",
                "waves": e2e_waves, "host_chunks": e2e_chunks,
+               "result_copy": f"copy kernel, {e2e_copy} blocks" if e2e_copy else "copy engines",
                "d2h_gbs": 4.0 * n_copy / (d0.elapsed_time(d1) * 1e-3) / 1e9}
         del rh, hits_h
 

@@ -172,6 +172,11 @@ typedef struct {
                                       instead of the hull of 32 hits' bands; 0: one queue for all.
                                       -1 (default): tile_d0 * 5 / 16, at least 3.  Reads back the value
                                       in use.  Same accumulators and records either way. */
+#define HT_OPT_HOST_COPY 23        /* ht_process with host results in page-locked host memory
+                                      (cudaHostAlloc, cudaHostRegister): n >= 1 (default 32) copies them
+                                      with a kernel of n 64-thread blocks beside the next wave's
+                                      kernels; 0, and pageable memory always, use the copy engines
+                                      (cudaMemcpyAsync).  0..4096; same bytes either way. */
 #define HT_OPT_WAVES 19            /* read-only: waves (kernel sequences over groups of events) of the
                                       last ht_process */
 #define HT_OPT_RECORD_BUDGET 18    /* device memory for those records in bytes (0 = 72 GB): a wave of

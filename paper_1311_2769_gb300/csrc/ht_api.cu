@@ -123,6 +123,7 @@ struct ht_ctx {
     int vote_items = 0;                    // band vote over (hit, column) items (1) or the hull of queued hits (0)
     int hit_staging = 0;                   // hull band vote: hits staged into shared memory by bulk copies
     int band_split = -1;                   // hull band vote: narrow-band queue threshold (-1 auto, 0 off)
+    int host_copy = 32;                    // host results in page-locked memory: copy-kernel blocks (0: the copy engine)
     int r_narrow = 0;                      // resolved threshold passed to the kernel
     bool r_stage = false;                  // staged variants prepared for the resolved tile
     int r_stage_blocks_per_sm = 1, r_stage_rec_blocks_per_sm = 1, r_stage_smem = 0;
@@ -1249,6 +1250,10 @@ int ht_set_option(ht_ctx* ctx, int32_t key, int64_t value) {
             if (value != 0 && value != 1) return fail(ctx, HT_ERR_INVALID_ARG, "hit staging must be 0 or 1");
             ctx->hit_staging = (int)value;
             break;
+        case HT_OPT_HOST_COPY:
+            if (value < 0 || value > 4096) return fail(ctx, HT_ERR_INVALID_ARG, "host copy must be in [0, 4096]");
+            ctx->host_copy = (int)value;
+            break;
         case HT_OPT_BAND_SPLIT:
             if (value < -1 || value > 256) return fail(ctx, HT_ERR_INVALID_ARG, "band split must be in [-1, 256]");
             ctx->band_split = (int)value;
@@ -1318,6 +1323,7 @@ int ht_get_option(ht_ctx* ctx, int32_t key, int64_t* value) {
         case HT_OPT_VOTE_ITEMS: *value = ctx->vote_items; break;
         case HT_OPT_HIT_STAGING: *value = ctx->r_stage ? 1 : 0; break;
         case HT_OPT_BAND_SPLIT: *value = ctx->r_narrow; break;
+        case HT_OPT_HOST_COPY: *value = ctx->host_copy; break;
         case HT_OPT_RECORD_BUDGET: *value = ctx->rec_budget; break;
         case HT_OPT_WAVES: *value = ctx->wave_start.empty() ? 0 : (int64_t)ctx->wave_start.size() - 1; break;
         default: return fail(ctx, HT_ERR_INVALID_ARG, "unknown option %d", key);
@@ -1438,6 +1444,32 @@ int ht_associate(ht_ctx* ctx, int32_t window, int64_t* peak_offsets, int32_t* hi
     CU(cudaStreamSynchronize(s));
     *n_pairs = total;
     if (total > cap) return fail(ctx, HT_ERR_OVERFLOW, "%lld pairs, cap %lld", (long long)total, (long long)cap);
+    return HT_OK;
+}
+
+// The device address of a page-locked host result array, for copies by
+// host_copy_kernel; nullptr for pageable memory (copied by the copy engine).
+static unsigned char* locked_addr(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<unsigned char*>(a.devicePointer) : nullptr;
+}
+
+// bytes [off, off + bytes) of a device result array into the host array `dst`
+// (device address `dst_dev` when page-locked and kernel copies are on)
+static int copy_out(ht_ctx* ctx, void* dst, unsigned char* dst_dev, const void* src, size_t off, size_t bytes,
+                    cudaStream_t s) {
+    if (bytes == 0) return HT_OK;
+    const unsigned char* from = static_cast<const unsigned char*>(src) + off;
+    if (dst_dev)
+        CU(launch_host_copy(dst_dev + off, from, bytes, ctx->host_copy, s));
+    else
+        CU(cudaMemcpyAsync(static_cast<unsigned char*>(dst) + off, from, bytes, cudaMemcpyDeviceToHost, s));
+    ++ctx->launches;
     return HT_OK;
 }
 
@@ -1570,6 +1602,9 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
         return HT_OK;
     }
     CU(cudaMemcpyAsync(ctx->h_pinned, ctx->d_scal + 6, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    unsigned char* dk_peaks = ctx->host_copy ? locked_addr(res->peaks) : nullptr;
+    unsigned char* dk_poff = ctx->host_copy ? locked_addr(res->peak_offsets) : nullptr;
+    unsigned char* dk_hidx = ctx->host_copy ? locked_addr(res->hit_idx) : nullptr;
     // stored peaks / pairs already on the host (wave by wave)
     int64_t p_done = 0, q_done = 0;
     if (pipe) {
@@ -1579,15 +1614,18 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
             const int64_t p_cur = std::min(ctx->h_wave[2 * w], pcap), q_cur = std::min(ctx->h_wave[2 * w + 1], qcap);
             CU(cudaStreamWaitEvent(cs, ctx->wave_ev[w], 0));
             if (p_cur > p_done) {
-                CU(cudaMemcpyAsync(res->peaks + p_done, peaks + p_done, (p_cur - p_done) * sizeof(ht_peak),
-                                   cudaMemcpyDeviceToHost, cs));
-                CU(cudaMemcpyAsync(res->peak_offsets + p_done, poff + p_done, (p_cur - p_done) * sizeof(int64_t),
-                                   cudaMemcpyDeviceToHost, cs));
+                st = copy_out(ctx, res->peaks, dk_peaks, peaks, p_done * sizeof(ht_peak),
+                              (p_cur - p_done) * sizeof(ht_peak), cs);
+                if (!st)
+                    st = copy_out(ctx, res->peak_offsets, dk_poff, poff, p_done * sizeof(int64_t),
+                                  (p_cur - p_done) * sizeof(int64_t), cs);
+                if (st) return st;
                 p_done = p_cur;
             }
             if (q_cur > q_done) {
-                CU(cudaMemcpyAsync(res->hit_idx + q_done, hidx + q_done, (q_cur - q_done) * sizeof(int32_t),
-                                   cudaMemcpyDeviceToHost, cs));
+                st = copy_out(ctx, res->hit_idx, dk_hidx, hidx, q_done * sizeof(int32_t),
+                              (q_cur - q_done) * sizeof(int32_t), cs);
+                if (st) return st;
                 q_done = q_cur;
             }
         }
@@ -1603,12 +1641,18 @@ int ht_process(ht_ctx* ctx, const ht_hits* hits, uint32_t threshold, int32_t win
     res->counts[1] = nq;
     const int64_t cp = std::min(np, pcap), cq = std::min(nq, qcap);
     // the rest (everything, without the wave copies) and the final row end
-    if (cp > p_done) CU(cudaMemcpyAsync(res->peaks + p_done, peaks + p_done, (cp - p_done) * sizeof(ht_peak),
-                                        cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(res->peak_offsets + std::min(p_done, cp), poff + std::min(p_done, cp),
-                       (cp + 1 - std::min(p_done, cp)) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (cq > q_done) CU(cudaMemcpyAsync(res->hit_idx + q_done, hidx + q_done, (cq - q_done) * sizeof(int32_t),
-                                        cudaMemcpyDeviceToHost, s));
+    if (cp > p_done) st = copy_out(ctx, res->peaks, dk_peaks, peaks, p_done * sizeof(ht_peak),
+                                   (cp - p_done) * sizeof(ht_peak), s);
+    const int64_t o0 = std::min(p_done, cp);
+    if (!st)
+        st = copy_out(ctx, res->peak_offsets, dk_poff, poff, o0 * sizeof(int64_t), (cp + 1 - o0) * sizeof(int64_t), s);
+    if (!st && cq > q_done)
+        st = copy_out(ctx, res->hit_idx, dk_hidx, hidx, q_done * sizeof(int32_t), (cq - q_done) * sizeof(int32_t), s);
+    if (st) {
+        cudaStreamSynchronize(s);
+        if (pipe) cudaStreamSynchronize(ctx->copy_stream);
+        return st;
+    }
     CU(cudaStreamSynchronize(s));
     if (pipe) CU(cudaStreamSynchronize(ctx->copy_stream));
     if (np > pcap || nq > qcap)

@@ -129,6 +129,8 @@ cudaError_t vote_prepare(int tile_phi, int nk, int smem_bytes, int variant);
 cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blocks, int variant);
 cudaError_t launch_finalize(int64_t* scal, cudaStream_t s);
 cudaError_t launch_publish(const int64_t* scal, int64_t* host, cudaStream_t s);
+// dst: device address of page-locked host memory
+cudaError_t launch_host_copy(void* dst, const void* src, size_t bytes, int blocks, cudaStream_t s);
 cudaError_t launch_vote(int tile_phi, const VoteParams& p, int grid, int threads, int smem, cudaStream_t s,
                         int variant);
 cudaError_t launch_validate(const float* x, const float* y, const int8_t* layer, int64_t n_hits,

@@ -2280,6 +2280,45 @@ __global__ void __launch_bounds__(256, 3) assoc_range_kernel(const AssocParams p
 }
 
 // counts[0..1] = {peaks, pairs of stored peaks + pairs of peaks beyond the cap}
+// Device-to-host copy of results into page-locked host memory by the SMs
+// (each thread moves 16-byte words, four in flight).  Straight after the
+// step's kernels the copy engines ran at a quarter of the host link's rate
+// or less, where SM stores kept it.  Blocks of 64 threads with few registers
+// fit beside the persistent vote and association blocks, so a wave's copy
+// overlaps the next wave's kernels.  Source and destination sharing their
+// offset mod 16 take the 16-byte path (a byte head and tail), mod 4 a
+// 4-byte path, otherwise bytes.
+__global__ void __launch_bounds__(64) host_copy_kernel(unsigned char* __restrict__ dst,
+                                                       const unsigned char* __restrict__ src, size_t n) {
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+    const uintptr_t mis = (uintptr_t)dst ^ (uintptr_t)src;
+    const int unit = (mis & 15) == 0 ? 16 : ((mis & 3) == 0 ? 4 : 1);
+    size_t head = (size_t)((unit - ((uintptr_t)dst & (unit - 1))) & (unit - 1));
+    if (head > n) head = n;
+    for (size_t i = tid; i < head; i += nth) dst[i] = src[i];
+    const size_t nv = (n - head) / unit;
+    if (unit == 16) {
+        uint4* d = reinterpret_cast<uint4*>(dst + head);
+        const uint4* v = reinterpret_cast<const uint4*>(src + head);
+        size_t i = tid;
+        for (; i + 3 * nth < nv; i += 4 * nth) {
+            const uint4 a = v[i], b = v[i + nth], c = v[i + 2 * nth], e = v[i + 3 * nth];
+            d[i] = a;
+            d[i + nth] = b;
+            d[i + 2 * nth] = c;
+            d[i + 3 * nth] = e;
+        }
+        for (; i < nv; i += nth) d[i] = v[i];
+    } else if (unit == 4) {
+        uint32_t* d = reinterpret_cast<uint32_t*>(dst + head);
+        const uint32_t* v = reinterpret_cast<const uint32_t*>(src + head);
+        for (size_t i = tid; i < nv; i += nth) d[i] = v[i];
+    } else {
+        for (size_t i = tid; i < nv; i += nth) dst[head + i] = src[head + i];
+    }
+    for (size_t i = head + nv * unit + tid; i < n; i += nth) dst[i] = src[i];
+}
+
 // The running totals after a wave, stored straight into pinned host memory
 // (device-accessible under unified addressing).  A 16-byte copy-engine copy
 // on the compute stream would wait behind the copy stream's result copies,
@@ -2465,6 +2504,13 @@ cudaError_t vote_occupancy(int tile_phi, int nk, int threads, int smem, int* blo
     void* f = vote_variant(tile_phi, nk, variant);
     if (!f) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, f, threads, smem);
+}
+
+cudaError_t launch_host_copy(void* dst, const void* src, size_t bytes, int blocks, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    host_copy_kernel<<<blocks, 64, 0, s>>>(static_cast<unsigned char*>(dst), static_cast<const unsigned char*>(src),
+                                           bytes);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_publish(const int64_t* scal, int64_t* host, cudaStream_t s) {

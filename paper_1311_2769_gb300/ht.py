@@ -51,6 +51,7 @@ HT_OPT_WAVES = 19
 HT_OPT_VOTE_ITEMS = 20
 HT_OPT_HIT_STAGING = 21
 HT_OPT_BAND_SPLIT = 22
+HT_OPT_HOST_COPY = 23
 HT_VOTE_POINT = 0
 HT_VOTE_RANGE = 1
 HT_VOTE_LINE = 2

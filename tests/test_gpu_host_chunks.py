@@ -78,3 +78,53 @@ def test_host_chunks_with_overflow(ht):
         ctx.set_option(ht.HT_OPT_HOST_CHUNKS, 0)
     assert ei.value.status == ht.HT_ERR_INVALID_ARG
     ctx.close()
+
+
+def _pinned_results(ht, pcap, qcap, shift=0):
+    """Results in page-locked host memory; `shift` bytes past a 16-byte
+    boundary (so the copy kernel takes its 4-byte or byte path)."""
+    rh = ht.Results.__new__(ht.Results)
+    rh.peak_cap, rh.pair_cap = pcap, qcap
+    raw = [torch.empty(n + 16, dtype=torch.uint8).pin_memory() for n in (pcap * 20, (pcap + 1) * 8, qcap * 4, 16)]
+    base = [r.data_ptr() + ((16 - r.data_ptr() % 16) % 16) + shift for r in raw[:3]] + [raw[3].data_ptr()]
+    rh._raw = raw
+    rh.struct = ht.HtResults(base[0], pcap, base[1], base[2], qcap, base[3], ht.HT_HOST)
+
+    def host():
+        import ctypes
+        n = [int(v) for v in np.ctypeslib.as_array((ctypes.c_int64 * 2).from_address(base[3]))]
+        npk = min(n[0], pcap)
+        pk = np.ctypeslib.as_array((ctypes.c_int32 * (5 * npk)).from_address(base[0])).copy()
+        po = np.ctypeslib.as_array((ctypes.c_int64 * (npk + 1)).from_address(base[1])).copy()
+        nh = int(po[-1]) if npk else 0
+        hi = np.ctypeslib.as_array((ctypes.c_int32 * max(nh, 1)).from_address(base[2]))[:nh].copy()
+        return n, pk.view(ht.PEAK_DTYPE).reshape(-1) if npk else pk, po, hi
+    rh.host = host
+    return rh
+
+
+@pytest.mark.parametrize("shift", [0, 4, 1])
+def test_pinned_host_results_by_kernel_or_copy_engine(ht, shift):
+    """Results copied into page-locked host memory by the copy kernel (32
+    blocks, the default, or one) or by the copy engines equal the device
+    results, for 1, 4 and 8 host chunks, at aligned and shifted destinations."""
+    w = synth.WORKLOADS["batch_4096_lognormal"]
+    b = synth.generate(w, n_events=29, first_event=11)
+    ctx = ht.Context(w.grid, w.spec.layers)
+    assert ctx.get_option(ht.HT_OPT_HOST_COPY) == 32
+    dev = ht.Results(1 << 21, 1 << 26, device="cuda")
+    ctx.process(ht.Hits.from_batch(b, device="cuda"), w.threshold, 1, dev)
+    ctx.sync()
+    pk, po, hi = dev.host()
+    for copy in (32, 1, 0):
+        ctx.set_option(ht.HT_OPT_HOST_COPY, copy)
+        for chunks in (1, 4, 8):
+            ctx.set_option(ht.HT_OPT_HOST_CHUNKS, chunks)
+            rh = _pinned_results(ht, 1 << 21, 1 << 26, shift)
+            ctx.process(ht.Hits.from_batch(b), w.threshold, 1, rh)
+            n, pk2, po2, hi2 = rh.host()
+            assert n == [len(pk), len(hi)]
+            assert np.array_equal(pk2, pk) and np.array_equal(po2, po) and np.array_equal(hi2, hi), (copy, chunks)
+    with pytest.raises(ht.HtError):
+        ctx.set_option(ht.HT_OPT_HOST_COPY, -1)
+    ctx.close()
