@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 # read + 1.322960 GB written; assoc_rec_kernel<4, 2>: 1.766159 + 0.443076 GB);
 # set to None when a kernel changes until it is captured again
 PROFILE_HITS = 275323
-VOTE_DRAM_PER_HIT = (0.164465 + 1.322960) * 1e9 / PROFILE_HITS
+VOTE_DRAM_PER_HIT = (0.081700 + 1.241773) * 1e9 / PROFILE_HITS
 ASSOC_DRAM_PER_HIT = (1.766159 + 0.443076) * 1e9 / PROFILE_HITS
 # FP32 lane operations per (hit, phi0, d0) cell of the method: 8 arithmetic
 # (q: 2 products and a difference; a = q - d; den: d^2 and 2dq terms, 3; the
