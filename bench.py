@@ -430,13 +430,15 @@ def _median_ms(fn, stream, flush, reps):
 
 
 def secondary_workloads(dev, stream, flush, reps=5):
-    """The dense single event (8.5k hits, 512 x 64 x 256 grid) and the pileup
-    batch (64 events of ~76k hits, 1024 x 128 x 512 grid, accumulators
-    admitted four events at a time), each timed as whole steps on the device
-    (median of `reps`, 3 for pileup, L2 flushed before each)."""
+    """The single 10-track event (150 hits, 64 x 8 x 64 grid), the dense
+    single event (8.5k hits, 512 x 64 x 256 grid) and the pileup batch (64
+    events of ~76k hits, 1024 x 128 x 512 grid, accumulators admitted four
+    events at a time), each timed as whole steps on the device (median of
+    `reps`, 21 for the small event, 3 for pileup, L2 flushed before each)."""
     from paper_1311_2769_gb300 import ht, synth
     out = {}
-    for name, waves_of, r in (("dense_event_500trk", 0, reps), ("pileup_64x5000trk", 4, 3)):
+    for name, waves_of, r in (("single_event_10trk", 0, 21), ("dense_event_500trk", 0, reps),
+                              ("pileup_64x5000trk", 4, 3)):
         w = synth.WORKLOADS[name]
         g = w.grid
         b = synth.generate(w)
